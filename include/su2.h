@@ -1,0 +1,245 @@
+/*
+ * su2.h -- C ABI of libsu2, a GB300 (sm_103a) implementation of the quenched
+ * SU(2) lattice gauge theory Monte Carlo of Cardoso & Bicudo, "SU(2) Lattice
+ * Gauge Theory Simulations on Fermi GPUs" (arXiv:1010.4834).
+ *
+ * The calls follow the paper's statement of the problem: start configurations
+ * (Section 4, kernel list: cold start, hot start, read a configuration), the
+ * checkerboard heat-bath update (Section 2, Eqs. 5-9 and 11; Section 4,
+ * "separately by direction and by even and odd sites"), over-relaxation
+ * (Section 2, Eq. 10) and the measurements: plaquette (Eqs. 12-13), Polyakov
+ * loop (Eqs. 14-15), Wilson loops (Eq. 18) and APE smearing (Eq. 19).
+ *
+ * Conventions
+ *   dims     (N0, N1, N2, N3) = (Nx, Ny, Nz, Nt); direction 3 is time.
+ *            Every extent is even and >= 2 (the checkerboard needs even
+ *            periodic extents); otherwise SU2_EINVAL.
+ *   site     s = x0 + N0*(x1 + N1*(x2 + N2*x3)); parity (x0+x1+x2+x3) mod 2.
+ *   link     quaternion (q0,q1,q2,q3) <-> q0*1 + i(q1 s1 + q2 s2 + q3 s3)
+ *            (Section 2, Eq. 1).
+ *   host     "canonical" host arrays are double[V][4][4]: site-major,
+ *            direction, quaternion component -- 16 doubles per site.
+ *   RNG      Philox4x32-10 keyed by (seed_lo, seed_hi); counter
+ *            (site, mu | lattice_id << 2, sweep, draw).  The hot start uses
+ *            sweep index 0xFFFFFFFF.  Heat-bath sweep i (counted from 0 since
+ *            the start) uses sweep index i, so a resumed chain replays the
+ *            same stream.
+ *   device   links live on the device in a structure of arrays: for each
+ *            direction mu and parity p, a contiguous array of the V/2 links
+ *            of that class, ordered by s >> 1.  Element: 2 x double2 (F64),
+ *            float4 (F32) or 4 x binary16 (F16Q, normalised in FP32 on load).
+ *
+ * Errors: every call returns an int status (SU2_OK = 0 on success).  No
+ * exception crosses the ABI.  su2_last_error() gives a message for the last
+ * failing call on the calling thread.  A failed call leaves the handle usable
+ * unless it returned SU2_ECUDA, in which case the CUDA context may be lost.
+ *
+ * Streams: each handle carries one CUDA stream (NULL -> a stream the library
+ * creates).  All device work of a call is enqueued on it in order.  Calls
+ * that return host values (measurements, get_links, sweep_count with device
+ * state) synchronise that stream before returning.
+ *
+ * Ownership: handles are owned by the library until su2_destroy /
+ * su2_batch_destroy.  Host arrays passed in are owned by the caller and only
+ * read or written during the call.  With su2_init_external the device buffer
+ * belongs to the caller and must outlive the handle.
+ *
+ * Threading: a handle must not be used from two threads at once.
+ */
+#ifndef SU2_H
+#define SU2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SU2_OK 0
+#define SU2_EINVAL 1   /* an argument is out of range                         */
+#define SU2_ENOMEM 2   /* device or host allocation failed / buffer too small */
+#define SU2_ECUDA 3    /* a CUDA call failed; see su2_last_error()            */
+#define SU2_ETIMEOUT 4 /* a bounded device-side wait gave up                  */
+#define SU2_ESTATE 5   /* call not valid in the handle's current state        */
+
+/* start configurations (Section 4, kernel list) */
+#define SU2_COLD 0 /* every link = 1                                          */
+#define SU2_HOT 1  /* every link Haar-random (Section 2, Eq. 4)               */
+
+/* link storage precision */
+#define SU2_F64 0  /* FP64 links, FP64 arithmetic                             */
+#define SU2_F32 1  /* FP32 links, FP32 arithmetic, FP64 reductions            */
+#define SU2_F16Q 2 /* binary16 quaternion storage, normalised on load, FP32   */
+
+/* a0 sampler for Section 2, Eq. 8 */
+#define SU2_SAMPLER_KP 0     /* Kennedy-Pendleton (default)                   */
+#define SU2_SAMPLER_CREUTZ 1 /* Creutz, the method the paper cites            */
+
+typedef struct su2_lattice su2_lattice;
+typedef struct su2_batch su2_batch;
+
+/* Thread-local message describing the last failure on this thread ("" if none). */
+const char* su2_last_error(void);
+
+/* Library version string. */
+const char* su2_version(void);
+
+/*
+ * Device bytes a lattice of these extents and precision needs: the link store,
+ * the two APE buffers (spatial links only) and reduction scratch.  For
+ * su2_init_external.  Returns SU2_EINVAL for bad extents or precision.
+ */
+int su2_required_bytes(const int dims[4], int prec, size_t* bytes);
+
+/*
+ * Create a lattice and initialise it (Section 4: cold or hot start).
+ * beta >= 0 (Section 2, Eq. 5: beta = 4/g0^2).  `cuda_stream` is a
+ * cudaStream_t or NULL (the library then creates its own stream).  The
+ * library allocates su2_required_bytes() of device memory.
+ */
+int su2_init(su2_lattice** h, const int dims[4], double beta, uint64_t seed, int start, int prec,
+             void* cuda_stream);
+
+/*
+ * As su2_init, but all device memory comes from the caller: `dev_buf` is a
+ * device pointer to `bytes` >= su2_required_bytes() bytes, 256-byte aligned,
+ * which the caller keeps alive until su2_destroy.  SU2_ENOMEM if too small.
+ */
+int su2_init_external(su2_lattice** h, const int dims[4], double beta, uint64_t seed, int start,
+                      int prec, void* dev_buf, size_t bytes, void* cuda_stream);
+
+/* Release the handle and any memory the library allocated for it.  NULL is a no-op. */
+int su2_destroy(su2_lattice* h);
+
+/* Replace the handle's stream (NULL -> the library's own stream). */
+int su2_set_stream(su2_lattice* h, void* cuda_stream);
+
+/*
+ * Sampler options.  max_tries >= 1 (default 64): trials of the a0 sampler per
+ * link before the old link is kept (an exact step: the accepted-value kernel is
+ * proportional to the target and independent of the old link).  max_tries = 1
+ * reproduces the paper's "only one try" benchmark mode (Section 5.1).
+ * sampler: SU2_SAMPLER_KP or SU2_SAMPLER_CREUTZ.
+ */
+int su2_set_options(su2_lattice* h, int max_tries, int sampler);
+
+/* Change beta (>= 0) for subsequent sweeps. */
+int su2_set_beta(su2_lattice* h, double beta);
+
+/*
+ * n >= 0 heat-bath sweeps.  One sweep = for mu = 0..3, for parity = 0, 1:
+ * update every link of direction mu on sites of that parity from its staple
+ * sum (Section 2, Eqs. 5-9, 11; Section 4).  Advances the sweep counter by n
+ * and invalidates the APE-smeared copy.  Stream-ordered, does not synchronise.
+ */
+int su2_heatbath_sweep(su2_lattice* h, int n);
+
+/*
+ * One checkerboard substep (direction mu in 0..3, parity in 0..1) of the heat
+ * bath with Philox sweep index `sweep`.  Does not change the sweep counter.
+ * Exposed for parity tests and custom schedules.
+ */
+int su2_heatbath_substep(su2_lattice* h, int mu, int parity, uint32_t sweep);
+
+/*
+ * n >= 0 over-relaxation sweeps, U -> W U^dagger W with W = Sigma/|Sigma|
+ * (Section 2, Eq. 10, read for the staple orientation of Eq. 11).  Same
+ * direction/parity order as the heat bath.  Deterministic; the sweep counter
+ * is unchanged.
+ */
+int su2_overrelax_sweep(su2_lattice* h, int n);
+
+/*
+ * Mean plaquette (Section 2, Eqs. 12-13), as the mean of (1/2) Re Tr of the
+ * plaquette: out[0] over all 6V plaquettes, out[1] over the 3V spatial ones,
+ * out[2] over the 3V space-time ones.  1 on the cold start; the paper's
+ * <P> per plaquette is 1 - out[0].  FP64 compensated accumulation.
+ * Synchronises.
+ */
+int su2_plaquette(su2_lattice* h, double out[3]);
+
+/*
+ * Signed Polyakov loop (Section 2, Eqs. 14-15): mean over the N0 N1 N2
+ * spatial sites of (1/2) Tr of the product of time links in increasing t.
+ * Synchronises.
+ */
+int su2_polyakov(su2_lattice* h, double* L);
+
+/*
+ * n >= 0 APE smearing steps with 0 <= alpha < 1 (Section 2, Eq. 19):
+ * U'_mu = P[(1-alpha) U_mu + (alpha/4) (sum of the four spatial staples)],
+ * spatial mu only, Jacobi update, P = normalisation.  The paper's w relates by
+ * w = alpha / (4 (1 - alpha)).  Writes the smeared copy; the Markov chain is
+ * untouched.  n = 0 makes the smeared copy equal to the current links.
+ */
+int su2_ape_smear(su2_lattice* h, double alpha, int n);
+
+/*
+ * Wilson loops (Section 2, Eq. 18): out[(R-1)*Tmax + (T-1)] for 1 <= R <= Rmax,
+ * 1 <= T <= Tmax, the mean over all sites and the three spatial directions of
+ * (1/2) Tr of the R x T loop.  1 <= Rmax <= min(N0,N1,N2), 1 <= Tmax <= N3,
+ * Rmax, Tmax <= 32.  use_smeared = 1 takes the spatial links from the last
+ * su2_ape_smear (SU2_ESTATE if there is none since the last sweep or
+ * set_links); temporal links are always the chain's.  Synchronises.
+ */
+int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smeared, double* out);
+
+/*
+ * Copy links to / from caller-owned host memory in the canonical FP64 layout
+ * (4V quaternions, 16 doubles per site).  set_links converts to the handle's
+ * precision (F16Q rounds to binary16), invalidates the smeared copy and keeps
+ * the sweep counter.  Both synchronise.
+ */
+int su2_get_links(su2_lattice* h, double* host);
+int su2_set_links(su2_lattice* h, const double* host);
+
+/* Sweep counter: heat-bath sweeps done since the start (or as set by set_sweep_count / load). */
+int su2_sweep_count(su2_lattice* h, uint64_t* n);
+int su2_set_sweep_count(su2_lattice* h, uint64_t n);
+
+/*
+ * Checkpoint (Section 4: "read a configuration from input file"): a binary
+ * file with a header (magic "SU2GB300", version, dims, beta, seed, sweep
+ * counter, precision, sampler options) followed by the canonical FP64 links.
+ * su2_load creates a new handle with precision `prec` (-1: as saved).
+ */
+int su2_save(su2_lattice* h, const char* path);
+int su2_load(su2_lattice** h, const char* path, int prec, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched lattices: n independent lattices with their own extents and beta,
+ * swept together.  Lattice i uses Philox lattice_id = i.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * dims: n x 4 extents (each lattice obeys the su2_init rules), betas: n
+ * couplings >= 0, 1 <= n <= 1023.  Cold or hot start per lattice.  prec: SU2_F32
+ * or SU2_F64 or SU2_F16Q.
+ */
+int su2_batch_init(su2_batch** b, int n, const int* dims, const double* betas, uint64_t seed,
+                   int start, int prec, void* cuda_stream);
+int su2_batch_destroy(su2_batch* b);
+int su2_batch_set_options(su2_batch* b, int max_tries, int sampler);
+
+/*
+ * n heat-bath sweeps of every lattice, in one persistent kernel launch per
+ * call (replayed from a CUDA graph).  Lattices advance independently; within
+ * a lattice the eight substeps are ordered by bounded device-side barriers.
+ * SU2_ETIMEOUT if a barrier gave up (the sweep results are then invalid).
+ */
+int su2_batch_sweep(su2_batch* b, int n);
+
+/* out[3*i + k]: su2_plaquette of lattice i.  Synchronises. */
+int su2_batch_plaquette(su2_batch* b, double* out);
+/* out[i]: su2_polyakov of lattice i.  Synchronises. */
+int su2_batch_polyakov(su2_batch* b, double* out);
+/* Canonical FP64 links of lattice i (V_i * 16 doubles).  Synchronises. */
+int su2_batch_get_links(su2_batch* b, int i, double* host);
+int su2_batch_set_links(su2_batch* b, int i, const double* host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SU2_H */

@@ -21,7 +21,7 @@ CREUTZ = 1
 
 class Chain(C.Structure):
     _fields_ = [("beta", C.c_double), ("seed", C.c_uint64), ("lattice_id", C.c_uint32),
-                ("max_tries", C.c_int), ("sampler", C.c_int), ("u24", C.c_int)]
+                ("max_tries", C.c_int), ("sampler", C.c_int), ("u23", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -46,6 +46,7 @@ def _load(path):
         "oracle_shift": (C.c_long, [C.c_int, _ip, C.c_long, C.c_int, C.c_int]),
         "oracle_init_cold": (None, [C.c_int, _ip, _dp]),
         "oracle_init_hot": (None, [C.c_int, _ip, C.POINTER(Chain), _dp]),
+        "oracle_hot_link": (None, [C.POINTER(Chain), C.c_long, C.c_int, _dp]),
         "oracle_staple": (None, [C.c_int, _ip, _dp, C.c_long, C.c_int, _dp]),
         "oracle_sample_a0": (C.c_int, [C.POINTER(Chain), C.c_double, C.c_long, C.c_int,
                                        C.c_uint32, _dp, _dp]),
@@ -98,8 +99,8 @@ def _dims(dims):
     return len(dims), arr
 
 
-def chain(beta, seed=1, lattice_id=0, max_tries=64, sampler=KP, u24=0):
-    return Chain(float(beta), int(seed), int(lattice_id), int(max_tries), int(sampler), int(u24))
+def chain(beta, seed=1, lattice_id=0, max_tries=64, sampler=KP, u23=0):
+    return Chain(float(beta), int(seed), int(lattice_id), int(max_tries), int(sampler), int(u23))
 
 
 def philox(ctr, key):
@@ -110,8 +111,8 @@ def philox(ctr, key):
     return [o[i] for i in range(4)]
 
 
-def u01(x, u24=0):
-    return lib().oracle_u01(int(x) & 0xFFFFFFFF, int(u24))
+def u01(x, u23=0):
+    return lib().oracle_u01(int(x) & 0xFFFFFFFF, int(u23))
 
 
 def qmul(a, b):
@@ -149,6 +150,12 @@ def init_hot(dims, ch):
     nd, d = _dims(dims)
     lib().oracle_init_hot(nd, d, C.byref(ch), _d(U))
     return U
+
+
+def hot_link(ch, s, mu):
+    o = np.empty(4)
+    lib().oracle_hot_link(C.byref(ch), int(s), int(mu), _d(o))
+    return o
 
 
 def staple(dims, U, s, mu):

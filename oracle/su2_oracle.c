@@ -50,10 +50,10 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 }
 
 /* uint32 -> uniform in the open interval (0,1): (x + 1/2) 2^-32, exact in
- * FP64.  The 24-bit variant ((x >> 8) + 1/2) 2^-24 is the resolution a
- * single-precision implementation uses. */
-double oracle_u01(uint32_t x, int u24) {
-  if (u24) return ldexp((double)(x >> 8) + 0.5, -24);
+ * FP64.  The 23-bit variant ((x >> 9) + 1/2) 2^-23 is the finest grid a
+ * binary32 value in (0,1) holds exactly up to 1 - 2^-24. */
+double oracle_u01(uint32_t x, int u23) {
+  if (u23) return ldexp((double)(x >> 9) + 0.5, -23);
   return ldexp((double)x + 0.5, -32);
 }
 
@@ -68,7 +68,7 @@ void oracle_draw(const oracle_chain* c, long s, int mu, uint32_t sweep, uint32_t
   key[0] = (uint32_t)(c->seed & 0xffffffffu);
   key[1] = (uint32_t)(c->seed >> 32);
   oracle_philox4x32_10(ctr, key, r);
-  for (int i = 0; i < 4; i++) u[i] = oracle_u01(r[i], c->u24);
+  for (int i = 0; i < 4; i++) u[i] = oracle_u01(r[i], c->u23);
 }
 
 /* ======================================================================== */
@@ -181,15 +181,16 @@ static void haar_from_uniforms(const double u[4], double q[4]) {
 /* Hot start: "random SU(2) matrix" on every link (Section 4, kernel list),
  * read as a Haar-distributed element per link, from Philox draw 0 of the
  * reserved sweep index 0xFFFFFFFF. */
+void oracle_hot_link(const oracle_chain* c, long s, int mu, double q[4]) {
+  double u[4];
+  oracle_draw(c, s, mu, 0xFFFFFFFFu, 0u, u);
+  haar_from_uniforms(u, q);
+}
+
 void oracle_init_hot(int nd, const int* dims, const oracle_chain* c, double* U) {
   long vol = oracle_volume(nd, dims);
-  for (long s = 0; s < vol; s++) {
-    for (int mu = 0; mu < nd; mu++) {
-      double u[4];
-      oracle_draw(c, s, mu, 0xFFFFFFFFu, 0u, u);
-      haar_from_uniforms(u, U + ((size_t)s * nd + mu) * 4);
-    }
-  }
+  for (long s = 0; s < vol; s++)
+    for (int mu = 0; mu < nd; mu++) oracle_hot_link(c, s, mu, U + ((size_t)s * nd + mu) * 4);
 }
 
 /* ======================================================================== */

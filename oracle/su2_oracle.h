@@ -40,7 +40,7 @@ typedef struct {
   uint32_t lattice_id;  /* batch member, 0 for a single lattice              */
   int max_tries;        /* cap on sampler trials, >= 1                       */
   int sampler;          /* ORACLE_KP or ORACLE_CREUTZ                        */
-  int u24;              /* 0: uniforms with 32-bit resolution, 1: 24-bit     */
+  int u23;              /* 0: uniforms with 32-bit resolution, 1: 23-bit     */
 } oracle_chain;
 
 /* Counts collected by a substep or sweep. */
@@ -53,7 +53,7 @@ typedef struct {
 
 /* --- random numbers ---------------------------------------------------- */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
-double oracle_u01(uint32_t x, int u24);
+double oracle_u01(uint32_t x, int u23);
 void oracle_draw(const oracle_chain* c, long s, int mu, uint32_t sweep, uint32_t draw,
                  double u[4]);
 
@@ -68,6 +68,8 @@ long oracle_shift(int nd, const int* dims, long s, int mu, int step);
 /* --- start configurations (Section 4, kernel list: cold / hot start) ---- */
 void oracle_init_cold(int nd, const int* dims, double* U);
 void oracle_init_hot(int nd, const int* dims, const oracle_chain* c, double* U);
+/* the hot-start value of the single link (s, mu) */
+void oracle_hot_link(const oracle_chain* c, long s, int mu, double q[4]);
 
 /* --- heat bath (Section 2, Eqs. 5-9 and 11) ----------------------------- */
 void oracle_staple(int nd, const int* dims, const double* U, long s, int mu, double out[4]);

@@ -1,0 +1,559 @@
+// C ABI of libsu2 (declared in include/su2.h): handle life cycle, device
+// memory carving, CUDA-graph replay of heat-bath sweeps, measurements and
+// checkpoint I/O for single lattices.  Batched lattices are in su2_batch.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "su2.h"
+#include "su2_internal.h"
+#include "su2_capi_util.h"
+
+using namespace su2;
+
+// ---------------------------------------------------------------------------
+// Thread-local last error
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+namespace su2 {
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+void clear_error() { g_err[0] = 0; }
+}  // namespace su2
+
+extern "C" const char* su2_last_error(void) { return g_err; }
+extern "C" const char* su2_version(void) { return "su2-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct su2_lattice {
+  int dims[4];
+  int prec;
+  double beta;
+  uint64_t seed;
+  int max_tries;
+  int sampler;
+  uint64_t sweep;
+  Geom g;
+  int device;
+  // device memory
+  void* base;
+  size_t bytes;
+  bool own_mem;
+  void* links;
+  void* ape[2];
+  Scratch scratch;
+  uint32_t* d_sweep;
+  unsigned long long* d_stats;
+  double* staging;
+  int64_t staging_sites;
+  double* h_out;  // pinned host results
+  // streams and the cached sweep graph
+  cudaStream_t stream;
+  bool own_stream;
+  cudaStream_t cap_stream;
+  cudaGraphExec_t graph;
+  int graph_sweeps;
+  int smeared;  // 0 none, 1 in ape[0], 2 in ape[1]
+};
+
+namespace {
+
+constexpr int kGraphSweeps = 8;
+constexpr int64_t kStagingSites = (int64_t)1 << 18;
+
+struct Layout {
+  size_t links, ape0, ape1, partials, counter, out, state, staging, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout layout_for(const int dims[4], int prec) {
+  const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+  const size_t lb = (size_t)link_bytes(prec);
+  Layout L;
+  size_t o = 0;
+  L.links = o; o = align256(o + 4 * (size_t)V * lb);
+  L.ape0 = o; o = align256(o + 3 * (size_t)V * lb);
+  L.ape1 = o; o = align256(o + 3 * (size_t)V * lb);
+  L.partials = o; o = align256(o + kScratchPartials * sizeof(double));
+  L.counter = o; o = align256(o + 64 * sizeof(unsigned int));
+  L.out = o; o = align256(o + kScratchOut * sizeof(double));
+  L.state = o; o = align256(o + 256);
+  const int64_t st = V < kStagingSites ? V : kStagingSites;
+  L.staging = o; o = align256(o + (size_t)st * 16 * sizeof(double));
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+namespace su2 {
+int check_dims(const int dims[4]) {
+  if (!dims) return fail(SU2_EINVAL, "dims is NULL");
+  int64_t V = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (dims[i] < 2 || (dims[i] & 1))
+      return fail(SU2_EINVAL, "extent %d = %d: every extent must be even and >= 2", i, dims[i]);
+    V *= dims[i];
+    if (V > ((int64_t)1 << 31) - 1) return fail(SU2_EINVAL, "lattice volume exceeds 2^31 - 1 sites");
+  }
+  return SU2_OK;
+}
+}  // namespace su2
+
+static int check_common(double beta, int start, int prec) {
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(SU2_EINVAL, "beta must be finite and >= 0");
+  if (start != SU2_COLD && start != SU2_HOT) return fail(SU2_EINVAL, "start must be SU2_COLD or SU2_HOT");
+  if (prec != SU2_F64 && prec != SU2_F32 && prec != SU2_F16Q) return fail(SU2_EINVAL, "unknown precision %d", prec);
+  return SU2_OK;
+}
+
+static LatticeView view(const su2_lattice* h) {
+  LatticeView v;
+  v.links = h->links;
+  v.g = h->g;
+  v.prec = h->prec;
+  return v;
+}
+
+static HBParams hb_params(const su2_lattice* h) {
+  HBParams hp;
+  hp.beta = h->beta;
+  hp.key.k0 = (uint32_t)(h->seed & 0xffffffffu);
+  hp.key.k1 = (uint32_t)(h->seed >> 32);
+  hp.lattice_tag = 0;
+  hp.max_tries = h->max_tries;
+  hp.sampler = h->sampler;
+  return hp;
+}
+
+static void drop_graph(su2_lattice* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->graph_sweeps = 0;
+}
+
+static int init_common(su2_lattice** out, const int dims[4], double beta, uint64_t seed, int start,
+                       int prec, void* dev_buf, size_t bytes, void* stream) {
+  clear_error();
+  if (!out) return fail(SU2_EINVAL, "handle pointer is NULL");
+  *out = nullptr;
+  int rc = check_dims(dims);
+  if (rc) return rc;
+  if ((rc = check_common(beta, start, prec))) return rc;
+  const Layout L = layout_for(dims, prec);
+  su2_lattice* h = new (std::nothrow) su2_lattice();
+  if (!h) return fail(SU2_ENOMEM, "host allocation failed");
+  std::memcpy(h->dims, dims, sizeof h->dims);
+  h->prec = prec;
+  h->beta = beta;
+  h->seed = seed;
+  h->max_tries = 64;
+  h->sampler = SU2_SAMPLER_KP;
+  h->sweep = 0;
+  h->g = make_geom(dims);
+  cudaGetDevice(&h->device);
+  if (dev_buf) {
+    if (bytes < L.total) {
+      delete h;
+      return fail(SU2_ENOMEM, "external buffer has %zu bytes, %zu needed", bytes, L.total);
+    }
+    if (((uintptr_t)dev_buf & 255) != 0) {
+      delete h;
+      return fail(SU2_EINVAL, "external buffer must be 256-byte aligned");
+    }
+    h->base = dev_buf;
+    h->own_mem = false;
+  } else {
+    cudaError_t e = cudaMalloc(&h->base, L.total);
+    if (e != cudaSuccess) {
+      delete h;
+      cudaGetLastError();
+      return fail(SU2_ENOMEM, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e));
+    }
+    h->own_mem = true;
+  }
+  h->bytes = L.total;
+  char* b = (char*)h->base;
+  h->links = b + L.links;
+  h->ape[0] = b + L.ape0;
+  h->ape[1] = b + L.ape1;
+  h->scratch.partials = (double*)(b + L.partials);
+  h->scratch.counter = (unsigned int*)(b + L.counter);
+  h->scratch.out = (double*)(b + L.out);
+  h->d_sweep = (uint32_t*)(b + L.state);
+  h->d_stats = (unsigned long long*)(b + L.state + 64);
+  h->staging = (double*)(b + L.staging);
+  const int64_t V = 2 * h->g.vh;
+  h->staging_sites = V < kStagingSites ? V : kStagingSites;
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+    h->own_stream = false;
+  } else {
+    SU2_CU_CLEAN(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), su2_destroy(h));
+    h->own_stream = true;
+  }
+  SU2_CU_CLEAN(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), su2_destroy(h));
+  SU2_CU_CLEAN(cudaMallocHost(&h->h_out, kScratchOut * sizeof(double)), su2_destroy(h));
+  SU2_CU_CLEAN(cudaMemsetAsync(b + L.counter, 0, L.out - L.counter, h->stream), su2_destroy(h));
+  SU2_CU_CLEAN(cudaMemsetAsync(b + L.state, 0, 256, h->stream), su2_destroy(h));
+  SU2_CU_CLEAN(launch_init(view(h), start, hb_params(h).key, 0u, h->stream), su2_destroy(h));
+  *out = h;
+  return SU2_OK;
+}
+
+extern "C" int su2_required_bytes(const int dims[4], int prec, size_t* bytes) {
+  clear_error();
+  int rc = check_dims(dims);
+  if (rc) return rc;
+  if (prec < 0 || prec > 2) return fail(SU2_EINVAL, "unknown precision %d", prec);
+  if (!bytes) return fail(SU2_EINVAL, "bytes is NULL");
+  *bytes = layout_for(dims, prec).total;
+  return SU2_OK;
+}
+
+extern "C" int su2_init(su2_lattice** h, const int dims[4], double beta, uint64_t seed, int start,
+                        int prec, void* cuda_stream) {
+  return init_common(h, dims, beta, seed, start, prec, nullptr, 0, cuda_stream);
+}
+
+extern "C" int su2_init_external(su2_lattice** h, const int dims[4], double beta, uint64_t seed,
+                                 int start, int prec, void* dev_buf, size_t bytes,
+                                 void* cuda_stream) {
+  if (!dev_buf) return fail(SU2_EINVAL, "dev_buf is NULL");
+  return init_common(h, dims, beta, seed, start, prec, dev_buf, bytes, cuda_stream);
+}
+
+extern "C" int su2_destroy(su2_lattice* h) {
+  clear_error();
+  if (!h) return SU2_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  if (h->h_out) cudaFreeHost(h->h_out);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  if (h->own_mem && h->base) cudaFree(h->base);
+  delete h;
+  return SU2_OK;
+}
+
+extern "C" int su2_set_stream(su2_lattice* h, void* cuda_stream) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  SU2_CU(cudaStreamSynchronize(h->stream));
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+    h->own_stream = false;
+  } else {
+    SU2_CU(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  return SU2_OK;
+}
+
+extern "C" int su2_set_options(su2_lattice* h, int max_tries, int sampler) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (max_tries < 1) return fail(SU2_EINVAL, "max_tries must be >= 1");
+  if (sampler != SU2_SAMPLER_KP && sampler != SU2_SAMPLER_CREUTZ) return fail(SU2_EINVAL, "unknown sampler %d", sampler);
+  h->max_tries = max_tries;
+  h->sampler = sampler;
+  drop_graph(h);
+  return SU2_OK;
+}
+
+extern "C" int su2_set_beta(su2_lattice* h, double beta) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(SU2_EINVAL, "beta must be finite and >= 0");
+  h->beta = beta;
+  drop_graph(h);
+  return SU2_OK;
+}
+
+// One sweep's eight substeps; sweep index = *d_sweep + off.
+static cudaError_t enqueue_sweep(su2_lattice* h, uint32_t off, cudaStream_t st) {
+  const LatticeView v = view(h);
+  const HBParams hp = hb_params(h);
+  for (int mu = 0; mu < 4; ++mu)
+    for (int p = 0; p < 2; ++p) {
+      cudaError_t e = launch_heatbath(v, mu, p, h->d_sweep, off, hp, nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+static int build_graph(su2_lattice* h) {
+  drop_graph(h);
+  cudaGraph_t graph;
+  SU2_CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < kGraphSweeps && e == cudaSuccess; ++i) e = enqueue_sweep(h, (uint32_t)i, h->cap_stream);
+  if (e == cudaSuccess) e = launch_add_u32(h->d_sweep, kGraphSweeps, h->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (e2 == cudaSuccess) cudaGraphDestroy(graph);
+    return fail(SU2_ECUDA, "sweep graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&h->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return fail(SU2_ECUDA, "sweep graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  h->graph_sweeps = kGraphSweeps;
+  return SU2_OK;
+}
+
+extern "C" int su2_heatbath_sweep(su2_lattice* h, int n) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (n < 0) return fail(SU2_EINVAL, "n must be >= 0");
+  if (h->sweep + (uint64_t)n >= 0xFFFFFFFFull) return fail(SU2_EINVAL, "sweep counter would reach the reserved index 2^32 - 1");
+  DeviceGuard dg(h->device);
+  if (n == 0) return SU2_OK;
+  int left = n;
+  if (left >= kGraphSweeps) {
+    if (!h->graph) {
+      int rc = build_graph(h);
+      if (rc) return rc;
+    }
+    while (left >= kGraphSweeps) {
+      SU2_CU(cudaGraphLaunch(h->graph, h->stream));
+      left -= kGraphSweeps;
+    }
+  }
+  for (int i = 0; i < left; ++i) SU2_CU(enqueue_sweep(h, (uint32_t)i, h->stream));
+  if (left) SU2_CU(launch_add_u32(h->d_sweep, (uint32_t)left, h->stream));
+  h->sweep += (uint64_t)n;
+  h->smeared = 0;
+  return SU2_OK;
+}
+
+extern "C" int su2_heatbath_substep(su2_lattice* h, int mu, int parity, uint32_t sweep) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (mu < 0 || mu > 3 || parity < 0 || parity > 1) return fail(SU2_EINVAL, "mu must be 0..3 and parity 0..1");
+  DeviceGuard dg(h->device);
+  SU2_CU(launch_heatbath(view(h), mu, parity, nullptr, sweep, hb_params(h), nullptr, h->stream));
+  h->smeared = 0;
+  return SU2_OK;
+}
+
+extern "C" int su2_overrelax_sweep(su2_lattice* h, int n) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (n < 0) return fail(SU2_EINVAL, "n must be >= 0");
+  DeviceGuard dg(h->device);
+  for (int i = 0; i < n; ++i)
+    for (int mu = 0; mu < 4; ++mu)
+      for (int p = 0; p < 2; ++p) SU2_CU(launch_overrelax(view(h), mu, p, h->stream));
+  if (n) h->smeared = 0;
+  return SU2_OK;
+}
+
+static int fetch_out(su2_lattice* h, int count, double* dst) {
+  SU2_CU(cudaMemcpyAsync(h->h_out, h->scratch.out, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  SU2_CU(cudaStreamSynchronize(h->stream));
+  std::memcpy(dst, h->h_out, count * sizeof(double));
+  return SU2_OK;
+}
+
+extern "C" int su2_plaquette(su2_lattice* h, double out[3]) {
+  clear_error();
+  if (!h || !out) return fail(SU2_EINVAL, "NULL argument");
+  DeviceGuard dg(h->device);
+  SU2_CU(launch_plaquette(view(h), h->scratch, h->stream));
+  return fetch_out(h, 3, out);
+}
+
+extern "C" int su2_polyakov(su2_lattice* h, double* L) {
+  clear_error();
+  if (!h || !L) return fail(SU2_EINVAL, "NULL argument");
+  DeviceGuard dg(h->device);
+  SU2_CU(launch_polyakov(view(h), h->scratch, h->stream));
+  return fetch_out(h, 1, L);
+}
+
+extern "C" int su2_ape_smear(su2_lattice* h, double alpha, int n) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (!(alpha >= 0.0 && alpha < 1.0)) return fail(SU2_EINVAL, "alpha must be in [0, 1)");
+  if (n < 0) return fail(SU2_EINVAL, "n must be >= 0");
+  DeviceGuard dg(h->device);
+  if (n == 0) {
+    SU2_CU(launch_copy_spatial(view(h), h->ape[0], h->stream));
+    h->smeared = 1;
+    return SU2_OK;
+  }
+  LatticeView src = view(h);
+  int cur = 0;
+  for (int i = 0; i < n; ++i) {
+    SU2_CU(launch_ape(src, h->ape[cur], alpha, h->stream));
+    src.links = h->ape[cur];
+    cur ^= 1;
+  }
+  h->smeared = (cur ^ 1) + 1;
+  return SU2_OK;
+}
+
+extern "C" int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smeared, double* out) {
+  clear_error();
+  if (!h || !out) return fail(SU2_EINVAL, "NULL argument");
+  const int rlim = h->dims[0] < h->dims[1] ? (h->dims[0] < h->dims[2] ? h->dims[0] : h->dims[2])
+                                           : (h->dims[1] < h->dims[2] ? h->dims[1] : h->dims[2]);
+  if (Rmax < 1 || Rmax > rlim || Rmax > 32) return fail(SU2_EINVAL, "Rmax must be in 1..min(N0,N1,N2,32)");
+  if (Tmax < 1 || Tmax > h->dims[3] || Tmax > 32) return fail(SU2_EINVAL, "Tmax must be in 1..min(N3,32)");
+  if (use_smeared && !h->smeared) return fail(SU2_ESTATE, "no smeared links since the last update");
+  DeviceGuard dg(h->device);
+  const void* spatial = use_smeared ? h->ape[h->smeared - 1] : h->links;
+  SU2_CU(launch_wilson(view(h), spatial, Rmax, Tmax, h->scratch, h->stream));
+  return fetch_out(h, Rmax * Tmax, out);
+}
+
+extern "C" int su2_get_links(su2_lattice* h, double* host) {
+  clear_error();
+  if (!h || !host) return fail(SU2_EINVAL, "NULL argument");
+  DeviceGuard dg(h->device);
+  const int64_t V = 2 * h->g.vh;
+  for (int64_t s0 = 0; s0 < V; s0 += h->staging_sites) {
+    const int64_t ns = V - s0 < h->staging_sites ? V - s0 : h->staging_sites;
+    SU2_CU(launch_to_canonical(view(h), h->staging, s0, ns, h->stream));
+    SU2_CU(cudaMemcpyAsync(host + 16 * s0, h->staging, (size_t)ns * 16 * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+  }
+  SU2_CU(cudaStreamSynchronize(h->stream));
+  return SU2_OK;
+}
+
+extern "C" int su2_set_links(su2_lattice* h, const double* host) {
+  clear_error();
+  if (!h || !host) return fail(SU2_EINVAL, "NULL argument");
+  DeviceGuard dg(h->device);
+  const int64_t V = 2 * h->g.vh;
+  for (int64_t s0 = 0; s0 < V; s0 += h->staging_sites) {
+    const int64_t ns = V - s0 < h->staging_sites ? V - s0 : h->staging_sites;
+    SU2_CU(cudaMemcpyAsync(h->staging, host + 16 * s0, (size_t)ns * 16 * sizeof(double),
+                           cudaMemcpyHostToDevice, h->stream));
+    SU2_CU(launch_from_canonical(view(h), h->staging, s0, ns, h->stream));
+  }
+  SU2_CU(cudaStreamSynchronize(h->stream));
+  h->smeared = 0;
+  return SU2_OK;
+}
+
+extern "C" int su2_sweep_count(su2_lattice* h, uint64_t* n) {
+  clear_error();
+  if (!h || !n) return fail(SU2_EINVAL, "NULL argument");
+  *n = h->sweep;
+  return SU2_OK;
+}
+
+extern "C" int su2_set_sweep_count(su2_lattice* h, uint64_t n) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (n >= 0xFFFFFFFFull) return fail(SU2_EINVAL, "sweep counter must be below 2^32 - 1");
+  DeviceGuard dg(h->device);
+  const uint32_t v = (uint32_t)n;
+  SU2_CU(cudaMemcpyAsync(h->d_sweep, &v, sizeof v, cudaMemcpyHostToDevice, h->stream));
+  SU2_CU(cudaStreamSynchronize(h->stream));
+  h->sweep = n;
+  return SU2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint files
+// ---------------------------------------------------------------------------
+namespace {
+struct FileHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t dims[4];
+  int32_t prec;
+  double beta;
+  uint64_t seed;
+  uint64_t sweep;
+  int32_t max_tries;
+  int32_t sampler;
+};
+}  // namespace
+
+extern "C" int su2_save(su2_lattice* h, const char* path) {
+  clear_error();
+  if (!h || !path) return fail(SU2_EINVAL, "NULL argument");
+  const int64_t V = 2 * h->g.vh;
+  std::vector<double> buf;
+  try {
+    buf.resize((size_t)V * 16);
+  } catch (...) {
+    return fail(SU2_ENOMEM, "host buffer for %lld sites", (long long)V);
+  }
+  int rc = su2_get_links(h, buf.data());
+  if (rc) return rc;
+  FileHeader fh;
+  std::memset(&fh, 0, sizeof fh);
+  std::memcpy(fh.magic, "SU2GB300", 8);
+  fh.version = 1;
+  for (int i = 0; i < 4; ++i) fh.dims[i] = h->dims[i];
+  fh.prec = h->prec;
+  fh.beta = h->beta;
+  fh.seed = h->seed;
+  fh.sweep = h->sweep;
+  fh.max_tries = h->max_tries;
+  fh.sampler = h->sampler;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(SU2_EINVAL, "cannot open %s for writing", path);
+  const bool ok = std::fwrite(&fh, sizeof fh, 1, f) == 1 &&
+                  std::fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+  if (std::fclose(f) != 0 || !ok) return fail(SU2_EINVAL, "short write to %s", path);
+  return SU2_OK;
+}
+
+extern "C" int su2_load(su2_lattice** out, const char* path, int prec, void* cuda_stream) {
+  clear_error();
+  if (!out || !path) return fail(SU2_EINVAL, "NULL argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(SU2_EINVAL, "cannot open %s", path);
+  FileHeader fh;
+  if (std::fread(&fh, sizeof fh, 1, f) != 1 || std::memcmp(fh.magic, "SU2GB300", 8) != 0 || fh.version != 1) {
+    std::fclose(f);
+    return fail(SU2_EINVAL, "%s is not a version-1 SU2GB300 checkpoint", path);
+  }
+  int dims[4] = {fh.dims[0], fh.dims[1], fh.dims[2], fh.dims[3]};
+  int rc = check_dims(dims);
+  if (rc) { std::fclose(f); return rc; }
+  const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+  std::vector<double> buf;
+  try {
+    buf.resize((size_t)V * 16);
+  } catch (...) {
+    std::fclose(f);
+    return fail(SU2_ENOMEM, "host buffer for %lld sites", (long long)V);
+  }
+  const bool ok = std::fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) return fail(SU2_EINVAL, "%s is truncated", path);
+  su2_lattice* h = nullptr;
+  rc = su2_init(&h, dims, fh.beta, fh.seed, SU2_COLD, prec < 0 ? fh.prec : prec, cuda_stream);
+  if (rc) return rc;
+  if ((rc = su2_set_options(h, fh.max_tries, fh.sampler)) || (rc = su2_set_links(h, buf.data())) ||
+      (rc = su2_set_sweep_count(h, fh.sweep))) {
+    su2_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SU2_OK;
+}

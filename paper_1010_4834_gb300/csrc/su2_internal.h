@@ -1,0 +1,63 @@
+// Internal host-side interface between the C ABI (su2_capi.cu) and the kernel
+// translation units.  Not installed; the public interface is include/su2.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "su2_device.cuh"
+
+namespace su2 {
+
+// Device-wide constants, queried once per device.
+struct DeviceInfo {
+  int sms;
+  int l2_bytes;
+};
+const DeviceInfo& device_info();
+
+// Geometry helper (host): fills a Geom for extents n[4].
+Geom make_geom(const int n[4]);
+
+// One lattice's device view: link store base pointer (precision-typed at the
+// launch), geometry, and the heat-bath parameters.
+struct LatticeView {
+  void* links;      // 8 classes of vh links
+  Geom g;
+  int prec;
+};
+
+// Reduction scratch carved from the handle's device memory.
+struct Scratch {
+  double* partials;      // >= kScratchPartials doubles
+  unsigned int* counter; // one zero-initialised ticket counter per reduction
+  double* out;           // >= kScratchOut doubles, results of the last reduction
+};
+constexpr size_t kScratchPartials = (size_t)1 << 20;  // 8 MiB of doubles
+constexpr size_t kScratchOut = 2048;
+size_t scratch_bytes();
+
+// --- launches (all stream-ordered, return cudaGetLastError()) ------------
+cudaError_t launch_init(const LatticeView& v, int start, PhiloxKey key, uint32_t lattice_tag,
+                        cudaStream_t st);
+cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint32_t* sweep_base,
+                            uint32_t sweep_off, const HBParams& hp, unsigned long long* stats,
+                            cudaStream_t st);
+cudaError_t launch_overrelax(const LatticeView& v, int mu, int parity, cudaStream_t st);
+cudaError_t launch_plaquette(const LatticeView& v, const Scratch& s, cudaStream_t st);
+cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t st);
+// APE: src has (at least) the 6 spatial classes; dst receives them.
+cudaError_t launch_ape(const LatticeView& src, void* dst, double alpha, cudaStream_t st);
+cudaError_t launch_copy_spatial(const LatticeView& src, void* dst, cudaStream_t st);
+// Wilson loops: spatial links from `spatial` (6 classes), time links from v.
+cudaError_t launch_wilson(const LatticeView& v, const void* spatial, int rmax, int tmax,
+                          const Scratch& s, cudaStream_t st);
+// Canonical FP64 host layout <-> device store, for sites [s0, s0 + ns).
+cudaError_t launch_to_canonical(const LatticeView& v, double* canon, int64_t s0, int64_t ns,
+                                cudaStream_t st);
+cudaError_t launch_from_canonical(const LatticeView& v, const double* canon, int64_t s0,
+                                  int64_t ns, cudaStream_t st);
+cudaError_t launch_add_u32(uint32_t* p, uint32_t v, cudaStream_t st);
+
+}  // namespace su2

@@ -1,0 +1,214 @@
+"""Python view of libsu2: `Lattice` and `Batch`.
+
+Thin marshalling over the C ABI of include/su2.h.  Every step of the Monte
+Carlo runs in the library's CUDA kernels; PyTorch only supplies device memory
+(the link store lives in a torch uint8 tensor handed to su2_init_external) and
+the CUDA stream (torch's current stream unless one is given).
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import check, dims_arg
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(int(s.cuda_stream))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Lattice:
+    """One SU(2) lattice with links on the GPU (see include/su2.h).
+
+    dims: (N0, N1, N2, N3), each even >= 2.  start: "cold" | "hot".
+    prec: "f64" | "f32" | "f16q".  Device memory comes from torch unless
+    torch_memory=False (the library then calls cudaMalloc itself).
+    """
+
+    def __init__(self, dims, beta, seed=1, start="cold", prec="f32", stream=None,
+                 torch_memory=True, _handle=None):
+        import torch
+        L = _lib.load()
+        self.dims = tuple(int(d) for d in dims)
+        self.prec = _lib.PREC[prec]
+        self._buf = None
+        self._stream = stream
+        h = C.c_void_p()
+        if _handle is not None:
+            h = _handle
+        elif torch_memory:
+            nbytes = C.c_size_t()
+            check(L.su2_required_bytes(dims_arg(self.dims), self.prec, C.byref(nbytes)))
+            self._buf = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+            check(L.su2_init_external(C.byref(h), dims_arg(self.dims), float(beta), int(seed),
+                                      _lib.START[start], self.prec, C.c_void_p(self._buf.data_ptr()),
+                                      nbytes.value, _stream_ptr(stream)))
+        else:
+            check(L.su2_init(C.byref(h), dims_arg(self.dims), float(beta), int(seed),
+                             _lib.START[start], self.prec, _stream_ptr(stream)))
+        self._h = h
+
+    @property
+    def volume(self):
+        return int(np.prod(self.dims))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            check(_lib.load().su2_destroy(self._h))
+            self._h = C.c_void_p()
+        self._buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- chain ------------------------------------------------------------
+    def set_options(self, max_tries=64, sampler="kp"):
+        s = {"kp": _lib.SAMPLER_KP, "creutz": _lib.SAMPLER_CREUTZ}.get(sampler, sampler)
+        check(_lib.load().su2_set_options(self._h, int(max_tries), int(s)))
+
+    def set_beta(self, beta):
+        check(_lib.load().su2_set_beta(self._h, float(beta)))
+
+    def sweep(self, n=1):
+        check(_lib.load().su2_heatbath_sweep(self._h, int(n)))
+
+    def substep(self, mu, parity, sweep_index):
+        check(_lib.load().su2_heatbath_substep(self._h, int(mu), int(parity), int(sweep_index)))
+
+    def overrelax(self, n=1):
+        check(_lib.load().su2_overrelax_sweep(self._h, int(n)))
+
+    @property
+    def sweep_count(self):
+        n = C.c_uint64()
+        check(_lib.load().su2_sweep_count(self._h, C.byref(n)))
+        return n.value
+
+    @sweep_count.setter
+    def sweep_count(self, n):
+        check(_lib.load().su2_set_sweep_count(self._h, int(n)))
+
+    # -- measurements -----------------------------------------------------
+    def plaquette(self):
+        out = np.empty(3)
+        check(_lib.load().su2_plaquette(self._h, _dptr(out)))
+        return out
+
+    def polyakov(self):
+        v = C.c_double()
+        check(_lib.load().su2_polyakov(self._h, C.byref(v)))
+        return v.value
+
+    def ape_smear(self, alpha, n):
+        check(_lib.load().su2_ape_smear(self._h, float(alpha), int(n)))
+
+    def wilson_loops(self, rmax, tmax, smeared=False):
+        out = np.empty((rmax, tmax))
+        check(_lib.load().su2_wilson_loops(self._h, int(rmax), int(tmax), int(bool(smeared)), _dptr(out)))
+        return out
+
+    # -- links ------------------------------------------------------------
+    def get_links(self, out=None):
+        """Canonical FP64 links, shape (V, 4, 4) = (site, direction, component)."""
+        if out is None:
+            out = np.empty((self.volume, 4, 4))
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.volume * 16
+        check(_lib.load().su2_get_links(self._h, _dptr(out)))
+        return out
+
+    def set_links(self, U):
+        U = np.ascontiguousarray(U, np.float64)
+        assert U.size == self.volume * 16
+        check(_lib.load().su2_set_links(self._h, _dptr(U)))
+
+    def save(self, path):
+        check(_lib.load().su2_save(self._h, str(path).encode()))
+
+    @classmethod
+    def load(cls, path, prec=-1, stream=None):
+        h = C.c_void_p()
+        p = _lib.PREC[prec] if prec != -1 else -1
+        check(_lib.load().su2_load(C.byref(h), str(path).encode(), int(p), _stream_ptr(stream)))
+        # dims/prec from the file header: read back via a small parse
+        import struct
+        with open(path, "rb") as f:
+            head = f.read(8 + 4 + 16 + 4)
+        dims = struct.unpack("<4i", head[12:28])
+        prec_saved = struct.unpack("<i", head[28:32])[0]
+        obj = cls.__new__(cls)
+        obj.dims = tuple(dims)
+        obj.prec = prec_saved if p == -1 else p
+        obj._buf = None
+        obj._stream = stream
+        obj._h = h
+        return obj
+
+
+class Batch:
+    """Many independent lattices swept together (su2_batch_* in include/su2.h)."""
+
+    def __init__(self, dims_list, betas, seed=1, start="hot", prec="f32", stream=None):
+        L = _lib.load()
+        self.dims = [tuple(int(d) for d in dd) for dd in dims_list]
+        n = len(self.dims)
+        flat = (C.c_int * (4 * n))(*[d for dd in self.dims for d in dd])
+        b = np.ascontiguousarray(betas, np.float64)
+        assert len(b) == n
+        h = C.c_void_p()
+        check(L.su2_batch_init(C.byref(h), n, flat, _dptr(b), int(seed), _lib.START[start],
+                               _lib.PREC[prec], _stream_ptr(stream)))
+        self._h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            check(_lib.load().su2_batch_destroy(self._h))
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, max_tries=64, sampler="kp"):
+        s = {"kp": _lib.SAMPLER_KP, "creutz": _lib.SAMPLER_CREUTZ}.get(sampler, sampler)
+        check(_lib.load().su2_batch_set_options(self._h, int(max_tries), int(s)))
+
+    def sweep(self, n=1):
+        check(_lib.load().su2_batch_sweep(self._h, int(n)))
+
+    def plaquette(self):
+        out = np.empty((self.n, 3))
+        check(_lib.load().su2_batch_plaquette(self._h, _dptr(out)))
+        return out
+
+    def polyakov(self):
+        out = np.empty(self.n)
+        check(_lib.load().su2_batch_polyakov(self._h, _dptr(out)))
+        return out
+
+    def get_links(self, i):
+        V = int(np.prod(self.dims[i]))
+        out = np.empty((V, 4, 4))
+        check(_lib.load().su2_batch_get_links(self._h, int(i), _dptr(out)))
+        return out
+
+    def set_links(self, i, U):
+        U = np.ascontiguousarray(U, np.float64)
+        check(_lib.load().su2_batch_set_links(self._h, int(i), _dptr(U)))

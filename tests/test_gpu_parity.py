@@ -1,0 +1,364 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Same seeded inputs on both sides; comparisons element by element.
+Tolerances:
+  * FP64 links: 1e-12 absolute per quaternion component (the heat-bath
+    per-link bar).  Rounding differs only in the order of a few FP64
+    operations and in libm vs CUDA transcendentals (both within a few ulp).
+  * FP32 links: 2e-5 absolute.  A binary32 heat-bath update carries a few
+    ulp (6e-8) of error per operation through ~100 dependent operations;
+    links whose accept/reject decision the oracle finds within 1e-4 of
+    flipping are compared only for validity (unit norm), since either
+    outcome is a correct draw.
+  * F16Q storage: 4e-3 absolute (binary16 rounding, 2^-11 relative, of each
+    component before the FP32 renormalisation on load).
+  * Measurements: FP64 1e-12, FP32 2e-6 absolute (means of values in [-1,1]).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1010_4834_gb300 import Batch, Lattice, SU2Error, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 2e-5, "f16q": 4e-3}
+MTOL = {"f64": 1e-12, "f32": 2e-6, "f16q": 2e-3}
+SHAPES = [(2, 2, 2, 2), (4, 4, 4, 4), (6, 4, 2, 10), (8, 8, 8, 8), (4, 6, 8, 2)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def u23(prec):
+    return 0 if prec == "f64" else 1
+
+
+def as_stored(U, prec):
+    """The values a store of this precision holds for U (what set_links keeps)."""
+    if prec == "f32":
+        return U.astype(np.float32).astype(np.float64)
+    if prec == "f16q":
+        q = U.astype(np.float16).astype(np.float64)
+        return q / np.linalg.norm(q, axis=-1, keepdims=True)
+    return U.copy()
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16q"])
+@pytest.mark.parametrize("dims", SHAPES)
+def test_start_configurations(dims, prec):
+    lat = Lattice(dims, 2.0, seed=5, start="cold", prec=prec)
+    U = lat.get_links()
+    assert np.array_equal(U, oracle.init_cold(list(dims)))
+    lat.close()
+    lat = Lattice(dims, 2.0, seed=0x123456789, start="hot", prec=prec)
+    ch = oracle.chain(2.0, seed=0x123456789, u23=u23(prec))
+    ref = oracle.init_hot(list(dims), ch)
+    got = lat.get_links()
+    assert np.abs(got - ref).max() < {"f64": 1e-14, "f32": 2e-6, "f16q": 4e-3}[prec]
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16q"])
+def test_set_get_roundtrip(prec):
+    dims = (4, 6, 2, 8)
+    U = inputs.random_field(dims, 3)
+    lat = Lattice(dims, 2.0, prec=prec)
+    lat.set_links(U)
+    got = lat.get_links()
+    if prec == "f64":
+        assert np.array_equal(got, U)
+    elif prec == "f32":
+        assert np.array_equal(got, as_stored(U, prec))
+    else:
+        # binary16 storage; the FP32 renormalisation on load adds ~1 ulp
+        assert np.abs(got - as_stored(U, prec)).max() < 5e-7
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+def substep_compare(dims, prec, beta, U0, mu, p, sweep, sampler="kp", max_tries=64, seed=7):
+    lat = Lattice(dims, beta, seed=seed, prec=prec)
+    lat.set_options(max_tries, sampler)
+    lat.set_links(U0)
+    lat.substep(mu, p, sweep)
+    got = lat.get_links()
+    lat.close()
+    ref = as_stored(U0, prec)
+    ch = oracle.chain(beta, seed=seed, max_tries=max_tries,
+                      sampler=oracle.KP if sampler == "kp" else oracle.CREUTZ, u23=u23(prec))
+    st, marg = oracle.substep(list(dims), ref, ch, sweep, mu, p, margins=True)
+    ok = marg[:, mu] >= (0 if prec == "f64" else 1e-4)
+    diff = np.abs(got - ref).max(axis=-1)          # (V, 4)
+    bad = np.argwhere((diff > TOL[prec]) & ok[:, None])
+    assert len(bad) == 0, (prec, dims, mu, p, len(bad), diff.max())
+    # undecided links are still valid SU(2) elements
+    n = np.linalg.norm(got.reshape(-1, 4), axis=-1)
+    assert np.abs(n - 1).max() < (1e-12 if prec == "f64" else 1e-5 if prec == "f32" else 2e-3)
+    return st, (~ok).sum()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dims", SHAPES)
+def test_heatbath_substep(dims, prec):
+    U0 = inputs.random_field(dims, 11)
+    undecided = 0
+    for mu in range(4):
+        for p in range(2):
+            _, u = substep_compare(dims, prec, 2.3, U0, mu, p, sweep=3 + mu)
+            undecided += u
+    assert undecided <= max(2, 0.002 * np.prod(dims) * 4)
+
+
+@pytest.mark.parametrize("sampler,max_tries,beta", [("creutz", 64, 1.7), ("kp", 1, 2.0), ("kp", 3, 0.3),
+                                                    ("kp", 64, 0.0), ("creutz", 2, 6.0)])
+def test_heatbath_sampler_options(sampler, max_tries, beta):
+    dims = (4, 4, 6, 4)
+    U0 = inputs.random_field(dims, 12)
+    st, _ = substep_compare(dims, "f64", beta, U0, 2, 1, sweep=9, sampler=sampler, max_tries=max_tries)
+    if beta == 0.0:
+        assert st.haar == st.updates
+    if max_tries == 1:
+        assert st.capped > 0                       # keep-old path exercised
+
+
+@pytest.mark.parametrize("start", ["cold", "hot"])
+def test_sweep_parity_fp64(start):
+    """Config: 8^4, beta = 2.4, seed 1: one and two full sweeps, per link 1e-12."""
+    dims = (8, 8, 8, 8)
+    lat = Lattice(dims, 2.4, seed=1, start=start, prec="f64")
+    ch = oracle.chain(2.4, seed=1)
+    U = oracle.init_hot(list(dims), ch) if start == "hot" else oracle.init_cold(list(dims))
+    for sw in range(2):
+        lat.sweep(1)
+        oracle.sweep(list(dims), U, ch, sw)
+        got = lat.get_links()
+        assert np.abs(got - U).max() < 1e-12, (start, sw, np.abs(got - U).max())
+    assert lat.sweep_count == 2
+    np.testing.assert_allclose(lat.plaquette(), oracle.plaquette(list(dims), U), atol=1e-12, rtol=0)
+    assert abs(lat.polyakov() - oracle.polyakov(list(dims), U)) < 1e-12
+    lat.close()
+
+
+def test_graph_replay_matches_single_sweeps():
+    dims = (4, 4, 4, 8)
+    a = Lattice(dims, 2.2, seed=3, start="hot", prec="f64")
+    b = Lattice(dims, 2.2, seed=3, start="hot", prec="f64")
+    a.sweep(19)                      # two graph replays of 8 + 3 direct sweeps
+    for _ in range(19):
+        b.sweep(1)
+    assert a.sweep_count == b.sweep_count == 19
+    assert np.array_equal(a.get_links(), b.get_links())
+    a.close()
+    b.close()
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16q"])
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 6, 2, 8), (6, 4, 4, 10)])
+def test_measurements(dims, prec):
+    U = inputs.random_field(dims, 21)
+    lat = Lattice(dims, 2.0, prec=prec)
+    lat.set_links(U)
+    ref = as_stored(U, prec)
+    np.testing.assert_allclose(lat.plaquette(), oracle.plaquette(list(dims), ref), atol=MTOL[prec], rtol=0)
+    assert abs(lat.polyakov() - oracle.polyakov(list(dims), ref)) < MTOL[prec]
+    rmax, tmax = min(dims[:3]), dims[3]
+    np.testing.assert_allclose(lat.wilson_loops(rmax, tmax), oracle.wilson_loops(list(dims), ref, rmax, tmax),
+                               atol=MTOL[prec] * 5, rtol=0)
+    lat.close()
+
+
+def test_measurements_on_thermalised_configuration():
+    dims = (8, 8, 8, 8)
+    lat = Lattice(dims, 2.5, seed=2, start="hot", prec="f64")
+    lat.sweep(20)
+    U = lat.get_links()
+    np.testing.assert_allclose(lat.plaquette(), oracle.plaquette(list(dims), U), atol=1e-12, rtol=0)
+    assert abs(lat.polyakov() - oracle.polyakov(list(dims), U)) < 1e-12
+    np.testing.assert_allclose(lat.wilson_loops(8, 8), oracle.wilson_loops(list(dims), U, 8, 8), atol=1e-12)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,alpha", [(0, 0.7), (1, 0.7), (3, 0.444), (25, 0.7)])
+def test_ape_and_smeared_wilson(prec, n, alpha):
+    dims = (4, 6, 4, 6)
+    U = inputs.random_field(dims, 31)
+    lat = Lattice(dims, 2.0, prec=prec)
+    lat.set_links(U)
+    with pytest.raises(SU2Error):
+        lat.wilson_loops(2, 2, smeared=True)      # nothing smeared yet: SU2_ESTATE
+    lat.ape_smear(alpha, n)
+    ref = oracle.ape_smear(list(dims), as_stored(U, prec), alpha, n)
+    got = lat.wilson_loops(4, 6, smeared=True)
+    exp = oracle.wilson_loops(list(dims), ref, 4, 6)
+    tol = 1e-12 if prec == "f64" else 2e-5
+    np.testing.assert_allclose(got, exp, atol=tol, rtol=0)
+    # the chain itself is untouched
+    np.testing.assert_allclose(lat.plaquette(), oracle.plaquette(list(dims), as_stored(U, prec)),
+                               atol=MTOL[prec], rtol=0)
+    lat.sweep(1)
+    with pytest.raises(SU2Error):
+        lat.wilson_loops(2, 2, smeared=True)      # a sweep invalidates the smeared copy
+    lat.close()
+
+
+def test_overrelaxation():
+    dims = (4, 4, 6, 4)
+    U = inputs.random_field(dims, 41)
+    lat = Lattice(dims, 2.0, prec="f64")
+    lat.set_links(U)
+    lat.overrelax(1)
+    ref = U.copy()
+    for mu in range(4):
+        for p in range(2):
+            oracle.overrelax_substep(list(dims), ref, mu, p)
+    assert np.abs(lat.get_links() - ref).max() < 1e-12
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+def test_argument_and_state_errors():
+    lat = Lattice((4, 4, 4, 4), 2.0, prec="f32")
+    for bad in [lambda: lat.wilson_loops(5, 2), lambda: lat.wilson_loops(2, 5), lambda: lat.wilson_loops(0, 1),
+                lambda: lat.ape_smear(1.0, 1), lambda: lat.ape_smear(0.5, -1), lambda: lat.sweep(-1),
+                lambda: lat.substep(4, 0, 0), lambda: lat.set_options(0, "kp"), lambda: lat.set_beta(-1.0)]:
+        with pytest.raises(SU2Error) as e:
+            bad()
+        assert e.value.code == 1
+    with pytest.raises(SU2Error):
+        Lattice((4, 4, 4, 5), 2.0)
+    lat.close()
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    dims = (4, 4, 4, 6)
+    a = Lattice(dims, 2.3, seed=9, start="hot", prec="f64")
+    a.sweep(3)
+    path = tmp_path / "ck.su2"
+    a.save(path)
+    a.sweep(4)
+    b = Lattice.load(path)
+    assert b.sweep_count == 3
+    b.sweep(4)
+    assert np.array_equal(a.get_links(), b.get_links())
+    a.close()
+    b.close()
+
+
+def test_library_allocated_memory_path():
+    dims = (4, 4, 4, 4)
+    a = Lattice(dims, 2.1, seed=4, start="hot", prec="f64", torch_memory=False)
+    b = Lattice(dims, 2.1, seed=4, start="hot", prec="f64")
+    a.sweep(2)
+    b.sweep(2)
+    assert np.array_equal(a.get_links(), b.get_links())
+    a.close()
+    b.close()
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_batched_sweep_parity(prec):
+    dims = [(4, 4, 4, 4), (6, 4, 4, 2), (2, 4, 6, 4), (8, 8, 8, 8)]
+    betas = [2.0, 2.5, 0.0, 2.7]
+    b = Batch(dims, betas, seed=13, start="hot", prec=prec)
+    nsw = 2 if prec == "f64" else 1
+    b.sweep(nsw)
+    for i, d in enumerate(dims):
+        ch = oracle.chain(betas[i], seed=13, lattice_id=i, u23=u23(prec))
+        U = oracle.init_hot(list(d), ch)
+        for sw in range(nsw):
+            oracle.sweep(list(d), U, ch, sw)
+        diff = np.abs(b.get_links(i) - U).max(axis=-1)
+        if prec == "f64":
+            assert diff.max() < 1e-12, (i, diff.max())
+        else:
+            # FP32 after a full sweep: a decision that rounding flips changes
+            # that link and, through the staples, a few later ones; all other
+            # links agree to FP32 accuracy.
+            assert (diff < TOL[prec]).mean() > 0.99, (i, (diff >= TOL[prec]).sum())
+    plq = b.plaquette()
+    pol = b.polyakov()
+    for i, d in enumerate(dims):
+        U = b.get_links(i)
+        np.testing.assert_allclose(plq[i], oracle.plaquette(list(d), U), atol=MTOL[prec], rtol=0)
+        assert abs(pol[i] - oracle.polyakov(list(d), U)) < MTOL[prec]
+    b.close()
+
+
+def test_batched_matches_single_lattice_chain():
+    dims = [(4, 4, 4, 4), (6, 6, 6, 4)]
+    b = Batch(dims, [2.2, 2.6], seed=21, start="hot", prec="f64")
+    b.sweep(3)
+    for i, d in enumerate(dims):
+        ch = oracle.chain([2.2, 2.6][i], seed=21, lattice_id=i)
+        U = oracle.init_hot(list(d), ch)
+        for sw in range(3):
+            oracle.sweep(list(d), U, ch, sw)
+        assert np.abs(b.get_links(i) - U).max() < 1e-12
+    b.close()
+
+
+def test_batched_barrier_timeout_is_reported():
+    """Fault injection on the host side: the barrier waits for one arrival
+    that never comes; every bounded wait runs out and the call reports
+    SU2_ETIMEOUT without hanging or faulting, and the GPU stays usable."""
+    os.environ["SU2_FAULT"] = "barrier"
+    try:
+        b = Batch([(4, 4, 4, 4)], [2.0], seed=1, start="cold", prec="f32")
+    finally:
+        del os.environ["SU2_FAULT"]
+    with pytest.raises(SU2Error) as e:
+        b.sweep(1)
+    assert e.value.code == 4
+    b.close()
+    lat = Lattice((4, 4, 4, 4), 2.0, prec="f32")
+    lat.sweep(1)
+    assert lat.plaquette()[0] < 1.0
+    lat.close()
+
+
+# ---------------------------------------------------------------------------
+def test_full_size_64_sampled():
+    """64^4 FP32 (the benchmark's lattice and launch configuration): hot start,
+    one heat-bath substep and the plaquette, checked on sampled links."""
+    dims = (64, 64, 64, 64)
+    beta = 2.6
+    lat = Lattice(dims, beta, seed=1, start="hot", prec="f32")
+    U0 = lat.get_links()
+    ch = oracle.chain(beta, seed=1, u23=1)
+    rng = np.random.default_rng(0)
+    V = 64 ** 4
+    for s in rng.integers(0, V, 300):
+        for mu in range(4):
+            assert np.abs(U0[s, mu] - oracle.hot_link(ch, s, mu)).max() < 2e-6
+    lat.substep(1, 1, 0)
+    U1 = lat.get_links()
+    x = lambda s: (s % 64 + s // 64 % 64 + s // 4096 % 64 + s // 262144) % 2
+    checked = 0
+    for s in rng.integers(0, V, 4000):
+        s = int(s)
+        if x(s) != 1:
+            assert np.array_equal(U1[s], U0[s])
+            continue
+        assert np.array_equal(U1[s, [0, 2, 3]], U0[s, [0, 2, 3]])
+        sig = oracle.staple(list(dims), U0, s, 1)
+        n, new, m = oracle.heatbath_link(ch, s, 1, 0, sig, U0[s, 1])
+        if m < 1e-4:
+            continue
+        assert np.abs(U1[s, 1] - new).max() < 2e-5, (s, U1[s, 1], new)
+        checked += 1
+    assert checked > 1500
+    p = lat.plaquette()
+    assert abs(p[0] - oracle.plaquette(list(dims), U1)[0]) < 2e-7
+    lat.close()

@@ -70,15 +70,15 @@ def test_u01_closed_form():
     assert oracle.u01(0) == 2.0 ** -33
     assert oracle.u01(0xFFFFFFFF) == 1.0 - 2.0 ** -33
     assert oracle.u01(0x80000000) == 0.5 + 2.0 ** -33
-    # 24-bit resolution: ((x >> 8) + 1/2) 2^-24
-    assert oracle.u01(0, 1) == 2.0 ** -25
-    assert oracle.u01(0xFFFFFFFF, 1) == 1.0 - 2.0 ** -25
-    assert oracle.u01(0x000000FF, 1) == 2.0 ** -25
+    # 23-bit resolution: ((x >> 9) + 1/2) 2^-23
+    assert oracle.u01(0, 1) == 2.0 ** -24
+    assert oracle.u01(0xFFFFFFFF, 1) == 1.0 - 2.0 ** -24
+    assert oracle.u01(0x000001FF, 1) == 2.0 ** -24
     rng = np.random.default_rng(3)
     for x in rng.integers(0, 2**32, 200):
         x = int(x)
         assert oracle.u01(x) == (x + 0.5) / 2.0 ** 32
-        assert oracle.u01(x, 1) == ((x >> 8) + 0.5) / 2.0 ** 24
+        assert oracle.u01(x, 1) == ((x >> 9) + 0.5) / 2.0 ** 23
 
 
 def test_draw_keying():
