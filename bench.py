@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Benchmark of the SU(2) heat-bath Monte Carlo on GB300.
+
+Workload (one "step"): the 64^4 FP32 configuration -- hot start, 100
+checkerboard heat-bath sweeps each followed by the plaquette and Polyakov
+loop, then 25 APE smearing steps (alpha = 0.7) and Wilson loops W(R,T) for
+R, T = 1..16 on the smeared spatial links.  Every step of it runs in libsu2's
+kernels.  Metric: heat-bath link updates per second (100 x 4V per step).
+The links (1.07 GB) are larger than L2 (129 MB), so no L2 flush is needed
+between steps.
+
+Printed as one JSON line (rank 0), with:
+  roofline      the heat-bath substep kernel (the dominant one): algorithmic
+                bytes per launch over its CUDA-event launch time, against the
+                measured HBM copy bandwidth of MEASURED_PEAKS.json;
+  cpu_baseline  the plain FP64 CPU oracle on this host, one substep of the
+                same 64^4 lattice (rank 0 at N = 1 only);
+  e2e           the same metric through the public API starting from a host
+                configuration in pinned memory (H2D and results D2H inside the
+                timed region);
+  fp64 / f16q / batched / sweep_only   sub-measurements beside the FP32 path.
+
+`--impl reference` times the CPU oracle as it stands (each step one
+heat-bath substep of the same 64^4 lattice) and prints the same line shape.
+Multi-GPU (torchrun): independent replicas, one lattice per rank (the
+method's lattices do not shard here), weak scaling, max time over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "heat-bath link updates/s"
+UNIT = "link updates/s"
+DIMS = (64, 64, 64, 64)
+BETA = 2.6
+SWEEPS = 100
+APE_STEPS, APE_ALPHA = 25, 0.7
+RMAX = TMAX = 16
+WORKLOAD = "su2_64^4_f32_beta2.6_hot_100sweeps_plaq_poly_ape25_W16x16"
+BATCH_SHAPES = [(8, 8, 8, 8)] * 16 + [(12, 12, 12, 12)] * 16 + [(16, 16, 16, 16)] * 16 + [(24, 24, 24, 6)] * 16
+
+
+def volume(d):
+    v = 1
+    for x in d:
+        v *= x
+    return v
+
+
+def config(n):
+    return {"workload": WORKLOAD, "lattice": "x".join(map(str, DIMS)), "beta": BETA, "start": "hot",
+            "links": "f32", "reductions": "f64", "sweeps_per_step": SWEEPS, "ape": [APE_STEPS, APE_ALPHA],
+            "wilson": [RMAX, TMAX], "sampler": "kennedy-pendleton, max_tries 64",
+            "l2": "inputs larger than L2 (1.07 GB links vs 129 MB L2), no flush",
+            "parallelism": "replicas%d" % n if n > 1 else "single"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.proc = None
+        self.dev = device_id
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.dev is not None:
+                cmd += ["-i", str(self.dev)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+                power.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def nvsmi_id(torch, dev):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def step(lat, hist):
+    """One pass of the whole hot path on the resident lattice."""
+    lat.restart("hot")
+    lat.sweep_measure(SWEEPS, hist)
+    lat.ape_smear(APE_ALPHA, APE_STEPS)
+    return lat.wilson_loops(RMAX, TMAX, smeared=True)
+
+
+def timed_sweeps(torch, lat, n, reps=3):
+    """Device time of n heat-bath sweeps (graph path), best of reps."""
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        lat.sweep(n)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        best = t if best is None else min(best, t)
+    return best
+
+
+def substep_launch_seconds(torch, lat, sweeps=4):
+    """Average CUDA-event duration of one heat-bath substep launch."""
+    times = []
+    for sw in range(sweeps):
+        for mu in range(4):
+            for p in range(2):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                lat.substep(mu, p, 1000 + sw)
+                b.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b) / 1e3)
+    return statistics.mean(times), len(times)
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in ("su2_device.cuh", "su2_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_1010_4834_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(updates_per_launch):
+    """DRAM bytes per heat-bath launch from the committed ncu summary, scaled
+    by updates; None if the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "hb_substep_f32.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != source_sha():
+        return None
+    try:
+        return float(vals["dram_bytes_per_update"]) * updates_per_launch
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline():
+    """The oracle as it stands (single thread, FP64) on one heat-bath substep
+    of the same 64^4 lattice."""
+    import oracle
+    ch = oracle.chain(BETA, seed=1)
+    U = oracle.init_hot(list(DIMS), ch)
+    t0 = time.perf_counter()
+    st = oracle.substep(list(DIMS), U, ch, 0, 0, 0)
+    t = time.perf_counter() - t0
+    return {"value": st.updates / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one heat-bath substep (mu=0, even sites: %d link updates) of the %s beta=2.6 "
+                      "hot-start lattice, plain FP64 C, single thread; %.1f s"
+                      % (st.updates, "x".join(map(str, DIMS)), t)}
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, lrank = dist_env()
+    torch.cuda.set_device(lrank)
+    # one dedicated stream: the library's launches and the timing events share it
+    with torch.cuda.stream(torch.cuda.Stream()):
+        run_gpu_on_stream(args)
+
+
+def run_gpu_on_stream(args):
+    import numpy as np
+    import torch
+    ws, rank, lrank = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(lrank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    else:
+        dist = None
+        torch.cuda.set_device(lrank)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_1010_4834_gb300 import build as su2_build
+    if rank == 0 or ws == 1:
+        su2_build.build()
+    barrier()
+    from paper_1010_4834_gb300 import Batch, Lattice, inputs, kernel_launches
+
+    V = volume(DIMS)
+    lat = Lattice(DIMS, BETA, seed=1 + rank, start="hot", prec="f32")
+    hist = np.empty((SWEEPS, 4))
+    for _ in range(args.warmup):
+        step(lat, hist)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(nvsmi_id(torch, lrank))
+    clocks.start()
+    n0 = kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        W = step(lat, hist)
+    ev1.record()
+    torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = kernel_launches() - n0
+    clk = clocks.stop()
+    barrier()
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        c = torch.tensor([launches], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        launches = int(c.item())
+    updates_per_step = SWEEPS * 4 * V
+    value = ws * updates_per_step * args.steps / elapsed
+    plaq_last = float(hist[-1, 0])
+
+    # roofline of the heat-bath substep (FP32: 8 links of 16 B per update)
+    t_launch, n_launch = substep_launch_seconds(torch, lat)
+    upd_launch = V // 2
+    alg_bytes = 8 * 16 * upd_launch
+    peaks, peak_kind = measured_peaks()
+    achieved = alg_bytes / t_launch / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_heatbath<F32>", "achieved": round(achieved, 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "peak_kind": peak_kind, "traffic": profiled_traffic(upd_launch),
+                "algorithmic_bytes_per_launch": alg_bytes, "launch_us": round(t_launch * 1e6, 2),
+                "launches_timed": n_launch, "updates_per_s_in_kernel": upd_launch / t_launch}
+
+    # end to end through the public API from a host configuration in pinned memory
+    host_cfg = torch.empty((V, 4, 4), dtype=torch.float64, pin_memory=True)
+    lat.get_links(host_cfg.numpy())
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.set_links(host_cfg.numpy())
+        lat.sweep_measure(SWEEPS, hist)
+        lat.ape_smear(APE_ALPHA, APE_STEPS)
+        W = lat.wilson_loops(RMAX, TMAX, smeared=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": ws * updates_per_step * e2e_steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": V * 16 * 8, "d2h_bytes_per_step": hist.nbytes + W.nbytes,
+           "path": "Lattice.set_links(pinned host links) -> sweep_measure(100) -> ape_smear(0.7, 25) -> "
+                   "wilson_loops(16, 16)", "steps": e2e_steps}
+    del host_cfg
+
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra["sweep_only"] = {"value": 20 * 4 * V / timed_sweeps(torch, lat, 20), "unit": UNIT,
+                               "what": "FP32 64^4 heat-bath sweeps alone (graph replay), 20 sweeps"}
+        lat.close()
+        del lat
+        for prec, n in (("f64", 4), ("f16q", 20)):
+            l2 = Lattice(DIMS, BETA, seed=1, start="hot", prec=prec)
+            l2.sweep(2)
+            extra[prec] = {"value": n * 4 * V / timed_sweeps(torch, l2, n, reps=2), "unit": UNIT,
+                           "what": "%s 64^4 heat-bath sweeps alone, %d sweeps" % (prec, n)}
+            l2.close()
+        betas = inputs.batch_betas(len(BATCH_SHAPES), seed=1)
+        b = Batch(BATCH_SHAPES, betas, seed=1, start="hot", prec="f32")
+        b.sweep(20)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        b.sweep(200)
+        e.record()
+        torch.cuda.synchronize()
+        tb = a.elapsed_time(e) / 1e3
+        vb = sum(volume(d) for d in BATCH_SHAPES)
+        extra["batched"] = {"value": 200 * 4 * vb / tb, "unit": UNIT,
+                            "what": "64 lattices (16 each of 8^4, 12^4, 16^4, 24^3x6), beta ~ U[2.0, 2.8], "
+                                    "FP32, 200 sweeps in one persistent cooperative launch (CUDA graph)",
+                            "ms_per_sweep": tb / 200 * 1e3}
+        b.close()
+    else:
+        lat.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (hot start from seed)",
+                "config": config(ws), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk, "plaquette_last": plaq_last}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the CPU oracle as it stands
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from oracle import build as oracle_build
+    oracle_build.build()
+    ch = oracle.chain(BETA, seed=1)
+    U = oracle.init_hot(list(DIMS), ch)
+    k = 0
+    for _ in range(args.warmup):
+        oracle.substep(list(DIMS), U, ch, k // 8, (k // 2) % 4, k % 2)
+        k += 1
+    t0 = time.perf_counter()
+    updates = 0
+    for _ in range(args.steps):
+        st = oracle.substep(list(DIMS), U, ch, k // 8, (k // 2) % 4, k % 2)
+        updates += st.updates
+        k += 1
+    t = time.perf_counter() - t0
+    value = updates / t
+    sample = ("each step one heat-bath substep (%d link updates) of the %s beta=2.6 hot-start lattice, "
+              "plain FP64 C oracle, single thread" % (volume(DIMS) // 2, "x".join(map(str, DIMS))))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (hot start from seed)",
+            "config": config(ws), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the FP64/F16Q/batched sub-measurements")
+    ap.add_argument("--extent", type=int, default=None,
+                    help="hypercubic extent override (small profiling cases only; not a bench line)")
+    ap.add_argument("--sweeps", type=int, default=None, help="sweeps per step override (profiling only)")
+    args = ap.parse_args()
+    global DIMS, SWEEPS, WORKLOAD
+    if args.extent:
+        DIMS = (args.extent,) * 4
+    if args.sweeps:
+        SWEEPS = args.sweeps
+    if args.extent or args.sweeps:
+        WORKLOAD = "profiling case %s, %d sweeps per step" % ("x".join(map(str, DIMS)), SWEEPS)
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -137,6 +137,23 @@ int su2_set_beta(su2_lattice* h, double beta);
 int su2_heatbath_sweep(su2_lattice* h, int n);
 
 /*
+ * Re-run the start configuration in place (Section 4: cold or hot start with
+ * the handle's seed), reset the sweep counter to 0 and drop the smeared copy.
+ * Stream-ordered, does not synchronise.
+ */
+int su2_restart(su2_lattice* h, int start);
+
+/*
+ * The Monte Carlo production loop: n >= 0 times (one heat-bath sweep, then
+ * su2_plaquette and su2_polyakov of the new configuration).  hist[4*i + k]
+ * receives, for sweep i of this call, the three plaquette means (k = 0..2)
+ * and the Polyakov loop (k = 3).  Results stay on the device until the end
+ * of the call (one synchronisation per 1024 sweeps).  Advances the sweep
+ * counter by n.
+ */
+int su2_sweep_measure(su2_lattice* h, int n, double* hist);
+
+/*
  * One checkerboard substep (direction mu in 0..3, parity in 0..1) of the heat
  * bath with Philox sweep index `sweep`.  Does not change the sweep counter.
  * Exposed for parity tests and custom schedules.
@@ -194,6 +211,12 @@ int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smeared, double
  */
 int su2_get_links(su2_lattice* h, double* host);
 int su2_set_links(su2_lattice* h, const double* host);
+
+/*
+ * Number of CUDA kernels this library has launched in this process (all
+ * handles; a replayed sweep graph counts each of its kernels).
+ */
+int su2_kernel_launches(uint64_t* n);
 
 /* Sweep counter: heat-bath sweeps done since the start (or as set by set_sweep_count / load). */
 int su2_sweep_count(su2_lattice* h, uint64_t* n);

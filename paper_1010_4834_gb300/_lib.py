@@ -47,6 +47,9 @@ SIGNATURES = {
     "su2_set_beta": (_i, [_vp, _d]),
     "su2_heatbath_sweep": (_i, [_vp, _i]),
     "su2_heatbath_substep": (_i, [_vp, _i, _i, _u32]),
+    "su2_restart": (_i, [_vp, _i]),
+    "su2_sweep_measure": (_i, [_vp, _i, _dp]),
+    "su2_kernel_launches": (_i, [C.POINTER(_u64)]),
     "su2_overrelax_sweep": (_i, [_vp, _i]),
     "su2_plaquette": (_i, [_vp, _dp]),
     "su2_polyakov": (_i, [_vp, _dp]),

@@ -42,17 +42,22 @@ def _stale():
     return os.path.getmtime(LIB) < max(os.path.getmtime(d) for d in deps)
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile libsu2.so if needed; return its path."""
-    if not force and not _stale():
+def build(force=False, verbose=False, extra_flags=(), out=None):
+    """Compile libsu2.so if needed; return its path.  `out` and `extra_flags`
+    build a separately named variant (used for tuning sweeps)."""
+    lib = out or LIB
+    if not force and out is None and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
+    tag = "" if out is None else "." + os.path.basename(out).replace(".so", "")
     nvcc = nvcc_path()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+    # -ftz=true: FP32 denormals flush to zero (link components and sums are
+    # O(1); it removes the denormal fix-ups around the SFU approximations).
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-ftz=true", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                      "-I", CSRC] + list(extra_flags)
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(OUT_DIR, os.path.basename(src) + tag + ".o")
         cmd = [nvcc] + common + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0 or verbose:
@@ -63,14 +68,14 @@ def build(force=False, verbose=False, extra_flags=()):
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("linking libsu2.so failed")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

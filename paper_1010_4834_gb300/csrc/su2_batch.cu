@@ -79,7 +79,8 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned long lon
 template <int P>
 __global__ void __launch_bounds__(256) k_batch_sweep(const BatchLattice* __restrict__ desc, int nlat,
                                                      int64_t total, int nsweeps,
-                                                     const uint32_t* sweep_base, HBParams hp,
+                                                     const uint32_t* sweep_base,
+                                                     const __grid_constant__ HBParams hp,
                                                      BarrierState* bs,
                                                      unsigned long long timeout_ns) {
   using R = typename Real<P>::T;
@@ -100,15 +101,18 @@ __global__ void __launch_bounds__(256) k_batch_sweep(const BatchLattice* __restr
           Links<P> L;
           L.p = reinterpret_cast<decltype(L.p)>(d.links);
           L.vh = d.g.vh;
-          const int64_t h = it - d.item_begin;
-          int x[4];
-          decode_half(d.g, (uint32_t)h, p, x);
-          const Quat<R> sig = staple<P, false>(L, d.g, x, h, mu, p, 0xF);
-          Quat<R> nl;
-          const uint32_t tag = (uint32_t)mu | ((uint32_t)l << 2);
-          const int n = heatbath_draw<R>(sig, make_uint4(site_of(d.g, x), tag, sweep0 + (uint32_t)sw, 0u),
-                                         hp, (R)d.beta, &nl);
-          if (n != 0) L.st(2 * mu + p, h, nl);
+          const int h = (int)(it - d.item_begin);
+          const Site x = site_from_half(d.g, (uint32_t)h, p);
+          HBParams lp = hp;
+          lp.lattice_tag = (uint32_t)l << 2;
+          const uint32_t sweep = sweep0 + (uint32_t)sw;
+          const R beta = (R)d.beta;
+          switch (mu) {
+            case 0: heatbath_site<P, 0, false>(L, d.g, x, h, p, sweep, lp, beta); break;
+            case 1: heatbath_site<P, 1, false>(L, d.g, x, h, p, sweep, lp, beta); break;
+            case 2: heatbath_site<P, 2, false>(L, d.g, x, h, p, sweep, lp, beta); break;
+            default: heatbath_site<P, 3, false>(L, d.g, x, h, p, sweep, lp, beta); break;
+          }
         }
         if (!grid_barrier(bs, timeout_ns)) return;
       }
@@ -170,11 +174,17 @@ LatticeView lview(const su2_batch* b, int i) {
   return v;
 }
 
+PhiloxKey batch_key(const su2_batch* b) {
+  PhiloxKey k;
+  k.k0 = (uint32_t)(b->seed & 0xffffffffu);
+  k.k1 = (uint32_t)(b->seed >> 32);
+  return k;
+}
+
 HBParams batch_hp(const su2_batch* b) {
   HBParams hp;
   hp.beta = 0.0;  // per lattice
-  hp.key.k0 = (uint32_t)(b->seed & 0xffffffffu);
-  hp.key.k1 = (uint32_t)(b->seed >> 32);
+  hp.rk = round_keys(batch_key(b));
   hp.lattice_tag = 0;
   hp.max_tries = b->max_tries;
   hp.sampler = b->sampler;
@@ -209,6 +219,7 @@ cudaError_t enqueue_batch_sweep(su2_batch* b, int n, cudaStream_t st) {
     default: e = cudaLaunchKernelEx(&cfg, k_batch_sweep<kF16Q>, d, nl, tot, n, (const uint32_t*)b->d_sweep, hp, b->d_bar, b->timeout_ns); break;
   }
   if (e != cudaSuccess) return e;
+  count_launches(1);
   return launch_add_u32(b->d_sweep, (uint32_t)n, st);
 }
 
@@ -297,7 +308,7 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   SU2_CU_CLEAN(cudaMemcpyAsync(b->d_bar, &bs, sizeof bs, cudaMemcpyHostToDevice, b->stream), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaMemsetAsync(b->d_sweep, 0, 64, b->stream), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaMemsetAsync(b->scratch.counter, 0, 64 * sizeof(unsigned int), b->stream), su2_batch_destroy(b));
-  const PhiloxKey key = batch_hp(b).key;
+  const PhiloxKey key = batch_key(b);
   for (int i = 0; i < n; ++i)
     SU2_CU_CLEAN(launch_init(lview(b, i), start, key, (uint32_t)i << 2, b->stream), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaStreamSynchronize(b->stream), su2_batch_destroy(b));
@@ -340,6 +351,7 @@ extern "C" int su2_batch_sweep(su2_batch* b, int n) {
   if (!b->graph || b->graph_n != n) {
     drop_graph(b);
     cudaGraph_t graph;
+    CaptureScope no_count;
     SU2_CU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_batch_sweep(b, n, b->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
@@ -356,6 +368,7 @@ extern "C" int su2_batch_sweep(su2_batch* b, int n) {
     b->graph_n = n;
   }
   SU2_CU(cudaGraphLaunch(b->graph, b->stream));
+  count_launches(2);
   b->sweep += (uint64_t)n;
   // The barrier flag is checked on the next synchronising call; check it
   // here too so a timed-out sweep is reported by the call that ran it.

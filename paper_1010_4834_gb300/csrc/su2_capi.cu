@@ -55,6 +55,7 @@ struct su2_lattice {
   Scratch scratch;
   uint32_t* d_sweep;
   unsigned long long* d_stats;
+  double* d_hist;
   double* staging;
   int64_t staging_sites;
   double* h_out;  // pinned host results
@@ -72,8 +73,10 @@ namespace {
 constexpr int kGraphSweeps = 8;
 constexpr int64_t kStagingSites = (int64_t)1 << 18;
 
+constexpr int kHistSweeps = 1024;
+
 struct Layout {
-  size_t links, ape0, ape1, partials, counter, out, state, staging, total;
+  size_t links, ape0, ape1, partials, counter, out, state, hist, staging, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -90,6 +93,7 @@ Layout layout_for(const int dims[4], int prec) {
   L.counter = o; o = align256(o + 64 * sizeof(unsigned int));
   L.out = o; o = align256(o + kScratchOut * sizeof(double));
   L.state = o; o = align256(o + 256);
+  L.hist = o; o = align256(o + (size_t)kHistSweeps * 4 * sizeof(double));
   const int64_t st = V < kStagingSites ? V : kStagingSites;
   L.staging = o; o = align256(o + (size_t)st * 16 * sizeof(double));
   L.total = o;
@@ -127,11 +131,17 @@ static LatticeView view(const su2_lattice* h) {
   return v;
 }
 
+static PhiloxKey philox_key(uint64_t seed) {
+  PhiloxKey k;
+  k.k0 = (uint32_t)(seed & 0xffffffffu);
+  k.k1 = (uint32_t)(seed >> 32);
+  return k;
+}
+
 static HBParams hb_params(const su2_lattice* h) {
   HBParams hp;
   hp.beta = h->beta;
-  hp.key.k0 = (uint32_t)(h->seed & 0xffffffffu);
-  hp.key.k1 = (uint32_t)(h->seed >> 32);
+  hp.rk = round_keys(philox_key(h->seed));
   hp.lattice_tag = 0;
   hp.max_tries = h->max_tries;
   hp.sampler = h->sampler;
@@ -194,6 +204,7 @@ static int init_common(su2_lattice** out, const int dims[4], double beta, uint64
   h->scratch.out = (double*)(b + L.out);
   h->d_sweep = (uint32_t*)(b + L.state);
   h->d_stats = (unsigned long long*)(b + L.state + 64);
+  h->d_hist = (double*)(b + L.hist);
   h->staging = (double*)(b + L.staging);
   const int64_t V = 2 * h->g.vh;
   h->staging_sites = V < kStagingSites ? V : kStagingSites;
@@ -208,7 +219,7 @@ static int init_common(su2_lattice** out, const int dims[4], double beta, uint64
   SU2_CU_CLEAN(cudaMallocHost(&h->h_out, kScratchOut * sizeof(double)), su2_destroy(h));
   SU2_CU_CLEAN(cudaMemsetAsync(b + L.counter, 0, L.out - L.counter, h->stream), su2_destroy(h));
   SU2_CU_CLEAN(cudaMemsetAsync(b + L.state, 0, 256, h->stream), su2_destroy(h));
-  SU2_CU_CLEAN(launch_init(view(h), start, hb_params(h).key, 0u, h->stream), su2_destroy(h));
+  SU2_CU_CLEAN(launch_init(view(h), start, philox_key(h->seed), 0u, h->stream), su2_destroy(h));
   *out = h;
   return SU2_OK;
 }
@@ -298,6 +309,7 @@ static cudaError_t enqueue_sweep(su2_lattice* h, uint32_t off, cudaStream_t st) 
 static int build_graph(su2_lattice* h) {
   drop_graph(h);
   cudaGraph_t graph;
+  CaptureScope no_count;
   SU2_CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < kGraphSweeps && e == cudaSuccess; ++i) e = enqueue_sweep(h, (uint32_t)i, h->cap_stream);
@@ -332,6 +344,7 @@ extern "C" int su2_heatbath_sweep(su2_lattice* h, int n) {
     }
     while (left >= kGraphSweeps) {
       SU2_CU(cudaGraphLaunch(h->graph, h->stream));
+      count_launches(8 * kGraphSweeps + 1);
       left -= kGraphSweeps;
     }
   }
@@ -339,6 +352,53 @@ extern "C" int su2_heatbath_sweep(su2_lattice* h, int n) {
   if (left) SU2_CU(launch_add_u32(h->d_sweep, (uint32_t)left, h->stream));
   h->sweep += (uint64_t)n;
   h->smeared = 0;
+  return SU2_OK;
+}
+
+extern "C" int su2_restart(su2_lattice* h, int start) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (start != SU2_COLD && start != SU2_HOT) return fail(SU2_EINVAL, "start must be SU2_COLD or SU2_HOT");
+  DeviceGuard dg(h->device);
+  SU2_CU(launch_init(view(h), start, philox_key(h->seed), 0u, h->stream));
+  SU2_CU(cudaMemsetAsync(h->d_sweep, 0, sizeof(uint32_t), h->stream));
+  h->sweep = 0;
+  h->smeared = 0;
+  return SU2_OK;
+}
+
+extern "C" int su2_sweep_measure(su2_lattice* h, int n, double* hist) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (n < 0) return fail(SU2_EINVAL, "n must be >= 0");
+  if (n > 0 && !hist) return fail(SU2_EINVAL, "hist is NULL");
+  if (h->sweep + (uint64_t)n >= 0xFFFFFFFFull) return fail(SU2_EINVAL, "sweep counter would reach the reserved index 2^32 - 1");
+  DeviceGuard dg(h->device);
+  const LatticeView v = view(h);
+  for (int c0 = 0; c0 < n; c0 += kHistSweeps) {
+    const int m = n - c0 < kHistSweeps ? n - c0 : kHistSweeps;
+    for (int i = 0; i < m; ++i) {
+      SU2_CU(enqueue_sweep(h, 0u, h->stream));
+      SU2_CU(launch_add_u32(h->d_sweep, 1u, h->stream));
+      Scratch sp = h->scratch;
+      sp.out = h->d_hist + 4 * i;
+      SU2_CU(launch_plaquette(v, sp, h->stream));
+      sp.out = h->d_hist + 4 * i + 3;
+      SU2_CU(launch_polyakov(v, sp, h->stream));
+    }
+    SU2_CU(cudaMemcpyAsync(hist + 4 * (size_t)c0, h->d_hist, (size_t)m * 4 * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+    SU2_CU(cudaStreamSynchronize(h->stream));
+  }
+  h->sweep += (uint64_t)n;
+  if (n) h->smeared = 0;
+  return SU2_OK;
+}
+
+extern "C" int su2_kernel_launches(uint64_t* n) {
+  clear_error();
+  if (!n) return fail(SU2_EINVAL, "n is NULL");
+  *n = launches_total();
   return SU2_OK;
 }
 

@@ -5,6 +5,10 @@
 // Paper: Cardoso & Bicudo, arXiv:1010.4834.  Section 2 (Eqs. 1-9, 11) defines
 // the link parametrisation and the heat-bath distribution; Section 4 the
 // checkerboard ("separately by direction and by even and odd sites").
+//
+// Coordinates are kept in scalars and every lattice shift names its direction
+// at compile time, so no coordinate array is ever indexed at run time (which
+// would put it in local memory).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -63,6 +67,21 @@ template <class R> __device__ __forceinline__ Quat<R> qmul_dn(const Quat<R>& a, 
   return r;
 }
 
+// s += a b^dagger and s += a b, each component one chain of fused multiply-adds.
+template <class R> __device__ __forceinline__ void qacc_mul_nd(Quat<R>& s, const Quat<R>& a, const Quat<R>& b) {
+  s.w = fma(a.w, b.w, fma(a.x, b.x, fma(a.y, b.y, fma(a.z, b.z, s.w))));
+  s.x = fma(-a.w, b.x, fma(a.x, b.w, fma(a.y, b.z, fma(-a.z, b.y, s.x))));
+  s.y = fma(-a.w, b.y, fma(a.y, b.w, fma(a.z, b.x, fma(-a.x, b.z, s.y))));
+  s.z = fma(-a.w, b.z, fma(a.z, b.w, fma(a.x, b.y, fma(-a.y, b.x, s.z))));
+}
+
+template <class R> __device__ __forceinline__ void qacc_mul(Quat<R>& s, const Quat<R>& a, const Quat<R>& b) {
+  s.w = fma(a.w, b.w, fma(-a.x, b.x, fma(-a.y, b.y, fma(-a.z, b.z, s.w))));
+  s.x = fma(a.w, b.x, fma(a.x, b.w, fma(-a.y, b.z, fma(a.z, b.y, s.x))));
+  s.y = fma(a.w, b.y, fma(a.y, b.w, fma(-a.z, b.x, fma(a.x, b.z, s.y))));
+  s.z = fma(a.w, b.z, fma(a.z, b.w, fma(-a.x, b.y, fma(a.y, b.x, s.z))));
+}
+
 template <class R> __device__ __forceinline__ R qdot(const Quat<R>& a, const Quat<R>& b) {
   return a.w * b.w + a.x * b.x + a.y * b.y + a.z * b.z;
 }
@@ -81,72 +100,122 @@ template <class R> __device__ __forceinline__ Quat<R> qone() { return qmake<R>(1
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Each round multiplies
 // counter words 0 and 2 by the round multipliers into 64-bit products, XORs
 // the high halves with the odd words and the round key, and permutes; the key
-// advances by the Weyl increments between rounds.
+// advances by the Weyl increments between rounds.  The ten round keys depend
+// only on the seed, so the host computes them once and the kernels read them
+// from their (constant-bank) parameters.
 // ---------------------------------------------------------------------------
 struct PhiloxKey { uint32_t k0, k1; };
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key) {
-  uint32_t k0 = key.k0, k1 = key.k1;
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline RoundKeys round_keys(PhiloxKey key) {
+  RoundKeys rk;
+  uint32_t a = key.k0, b = key.k1;
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = a;
+    rk.k1[r] = b;
+    a += 0x9E3779B9u;
+    b += 0xBB67AE85u;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, const RoundKeys& rk) {
 #pragma unroll
-  for (int round = 0; round < 10; ++round) {
+  for (int r = 0; r < 10; ++r) {
     const uint64_t m0 = (uint64_t)0xD2511F53u * c.x;
     const uint64_t m1 = (uint64_t)0xCD9E8D57u * c.z;
-    const uint32_t nx = (uint32_t)(m1 >> 32) ^ c.y ^ k0;
-    const uint32_t nz = (uint32_t)(m0 >> 32) ^ c.w ^ k1;
+    const uint32_t nx = (uint32_t)(m1 >> 32) ^ c.y ^ rk.k0[r];
+    const uint32_t nz = (uint32_t)(m0 >> 32) ^ c.w ^ rk.k1[r];
     c.y = (uint32_t)m1;
     c.w = (uint32_t)m0;
     c.x = nx;
     c.z = nz;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return c;
 }
 
 // uint32 -> uniform in (0,1).  FP64: (x + 1/2) 2^-32, exact.  FP32:
 // ((x >> 9) + 1/2) 2^-23, exact in binary32 (23-bit resolution keeps the
-// value strictly below 1).
-__device__ __forceinline__ double u01d(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
-__device__ __forceinline__ float u01f(uint32_t x) { return ((float)(x >> 9) + 0.5f) * 0x1p-23f; }
-
+// value strictly below 1).  The FP32 value is built without an int-to-float
+// conversion: the bit pattern 0x3F800000 | (x >> 9) is 1 + k 2^-23 with
+// k = x >> 9, so subtracting 1 (exact) and adding 2^-24 (exact, k + 1/2 needs
+// 24 significant bits) gives (k + 1/2) 2^-23.
 template <class R> __device__ __forceinline__ R u01(uint32_t x);
-template <> __device__ __forceinline__ double u01<double>(uint32_t x) { return u01d(x); }
-template <> __device__ __forceinline__ float u01<float>(uint32_t x) { return u01f(x); }
+template <> __device__ __forceinline__ double u01<double>(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
+template <> __device__ __forceinline__ float u01<float>(uint32_t x) {
+  return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.0f) + 0x1p-24f;
+}
 
-// Transcendentals per precision (library calls, no hand-written math).
-__device__ __forceinline__ double rlog(double v) { return log(v); }
-__device__ __forceinline__ float rlog(float v) { return logf(v); }
-__device__ __forceinline__ double sqrt_r(double v) { return sqrt(v); }
-__device__ __forceinline__ float sqrt_r(float v) { return sqrtf(v); }
-__device__ __forceinline__ void rsincospi(double v, double* s, double* c) { sincospi(v, s, c); }
-__device__ __forceinline__ void rsincospi(float v, float* s, float* c) { sincospif(v, s, c); }
-__device__ __forceinline__ double rcospi(double v) { return cospi(v); }
-__device__ __forceinline__ float rcospi(float v) { return cospif(v); }
-__device__ __forceinline__ double rexp(double v) { return exp(v); }
-__device__ __forceinline__ float rexp(float v) { return expf(v); }
-__device__ __forceinline__ double rmax0(double v) { return fmax(v, 0.0); }
-__device__ __forceinline__ float rmax0(float v) { return fmaxf(v, 0.0f); }
+// ---------------------------------------------------------------------------
+// Math policy.  FP64 calls the accurate CUDA functions (the FP64 path is the
+// one compared link by link with the oracle).  FP32 uses the SFU
+// approximations where their error (a few 1e-7) is below the FP32 resolution
+// of the result: log (max abs error 2^-21.4 on [0.5, 2], 3 ulp elsewhere),
+// sin/cos of an argument reduced to [-pi, pi] by cos(2 pi u) =
+// -cos(2 pi (u - 1/2)), reciprocal square root; the Box-Muller radius keeps the
+// accurate logf, because there ln(u) -> 0 as u -> 1 and an absolute error
+// would dominate it.
+// ---------------------------------------------------------------------------
+template <class R> struct Math;
+
+template <> struct Math<double> {
+  static __device__ __forceinline__ double log_fast(double v) { return log(v); }
+  static __device__ __forceinline__ double log_acc(double v) { return log(v); }
+  static __device__ __forceinline__ double cos2pi(double u) { return cospi(2.0 * u); }
+  static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
+  static __device__ __forceinline__ double sqrt0(double v) { return sqrt(fmax(v, 0.0)); }
+  static __device__ __forceinline__ double rsqrt(double v) { return 1.0 / sqrt(v); }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double exp(double v) { return ::exp(v); }
+  static constexpr double kTiny = 1e-300;
+};
+
+template <> struct Math<float> {
+  static __device__ __forceinline__ float log_fast(float v) { return __logf(v); }
+  static __device__ __forceinline__ float log_acc(float v) { return logf(v); }
+  static __device__ __forceinline__ float cos2pi(float u) {
+    return -__cosf(6.28318530717958647692f * (u - 0.5f));
+  }
+  static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c) {
+    float ss, cc;
+    __sincosf(6.28318530717958647692f * (u - 0.5f), &ss, &cc);
+    *s = -ss;
+    *c = -cc;
+  }
+  static __device__ __forceinline__ float sqrt0(float v) {
+    v = fmaxf(v, 0.0f);
+    return v * rsqrtf(fmaxf(v, 1e-30f));
+  }
+  static __device__ __forceinline__ float rsqrt(float v) { return rsqrtf(v); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float exp(float v) { return __expf(v); }
+  static constexpr float kTiny = 1e-30f;
+};
 
 // Uniformly random unit quaternion (Haar measure, Section 2 Eq. 4) from four
 // uniforms: two Box-Muller pairs give four normals, normalised onto S^3.
 template <class R> __device__ __forceinline__ Quat<R> haar_from(uint4 r) {
+  using M = Math<R>;
   const R u0 = u01<R>(r.x), u1 = u01<R>(r.y), u2 = u01<R>(r.z), u3 = u01<R>(r.w);
-  const R a = sqrt_r(R(-2) * rlog(u0));
-  const R b = sqrt_r(R(-2) * rlog(u2));
+  const R a = M::sqrt0(R(-2) * M::log_acc(u0));
+  const R b = M::sqrt0(R(-2) * M::log_acc(u2));
   R s1, c1, s3, c3;
-  rsincospi(R(2) * u1, &s1, &c1);
-  rsincospi(R(2) * u3, &s3, &c3);
+  M::sincos2pi(u1, &s1, &c1);
+  M::sincos2pi(u3, &s3, &c3);
   Quat<R> z = qmake<R>(a * c1, a * s1, b * c3, b * s3);
-  const R inv = R(1) / sqrt_r(qdot(z, z));
-  return qscale(z, inv);
+  return qscale(z, M::rsqrt(qdot(z, z)));
 }
 
 // ---------------------------------------------------------------------------
-// Heat-bath parameters shared by a launch.
+// Heat-bath parameters shared by a launch (passed as a __grid_constant__
+// kernel parameter).
 // ---------------------------------------------------------------------------
 struct HBParams {
   double beta;
-  PhiloxKey key;
+  RoundKeys rk;
   uint32_t lattice_tag;  // lattice_id << 2 (ORed with mu in counter word 1)
   int max_tries;
   int sampler;           // 0 Kennedy-Pendleton, 1 Creutz
@@ -159,21 +228,22 @@ struct HBParams {
 //   Creutz:            a0 = 1 + ln(e^{-2 alpha} + (1 - e^{-2 alpha}) u0)/alpha,
 //                      accept if u1^2 <= 1 - a0^2.
 template <class R>
-__device__ __forceinline__ int sample_a0(R alpha, uint4 ctr, PhiloxKey key, int max_tries,
-                                         int sampler, R* a0) {
-  const R inv2a = R(0.5) / alpha;
-  const R e = sampler ? rexp(R(-2) * alpha) : R(0);
-  for (int n = 1; n <= max_tries; ++n) {
+__device__ __forceinline__ int sample_a0(R alpha, uint4 ctr, const HBParams& hp, R* a0) {
+  using M = Math<R>;
+  const R inv2a = M::div(R(0.5), alpha);
+  const int sampler = hp.sampler;
+  const R e = sampler ? M::exp(R(-2) * alpha) : R(0);
+  for (int n = 1; n <= hp.max_tries; ++n) {
     ctr.w = (uint32_t)n;
-    const uint4 r = philox4x32_10(ctr, key);
+    const uint4 r = philox(ctr, hp.rk);
     if (sampler == 0) {
       const R u0 = u01<R>(r.x), u1 = u01<R>(r.y), u2 = u01<R>(r.z), u3 = u01<R>(r.w);
-      const R c = rcospi(R(2) * u1);
-      const R delta = -(rlog(u0) + c * c * rlog(u2)) * inv2a;
+      const R c = M::cos2pi(u1);
+      const R delta = -(M::log_fast(u0) + c * c * M::log_fast(u2)) * inv2a;
       if (u3 * u3 <= R(1) - delta) { *a0 = R(1) - R(2) * delta; return n; }
     } else {
       const R u0 = u01<R>(r.x), u1 = u01<R>(r.y);
-      const R cand = R(1) + rlog(e + (R(1) - e) * u0) / alpha;
+      const R cand = R(1) + M::div(M::log_fast(e + (R(1) - e) * u0), alpha);
       if (u1 * u1 <= R(1) - cand * cand) { *a0 = cand; return n; }
     }
   }
@@ -188,26 +258,26 @@ __device__ __forceinline__ int sample_a0(R alpha, uint4 ctr, PhiloxKey key, int 
 template <class R>
 __device__ __forceinline__ int heatbath_draw(const Quat<R>& sigma, uint4 ctr, const HBParams& hp,
                                              R beta, Quat<R>* out) {
+  using M = Math<R>;
   const R k2 = qdot(sigma, sigma);
-  const R k = sqrt_r(k2);
-  const R alpha = beta * k;
+  const R invk = M::rsqrt(k2);
+  const R alpha = beta * k2 * invk;
   if (!(alpha >= R(1e-12))) {
     ctr.w = 1u;
-    *out = haar_from<R>(philox4x32_10(ctr, hp.key));
+    *out = haar_from<R>(philox(ctr, hp.rk));
     return -1;
   }
   R a0;
-  const int n = sample_a0<R>(alpha, ctr, hp.key, hp.max_tries, hp.sampler, &a0);
+  const int n = sample_a0<R>(alpha, ctr, hp, &a0);
   if (n == 0) return 0;
   ctr.w = 0u;
-  const uint4 r = philox4x32_10(ctr, hp.key);
+  const uint4 r = philox(ctr, hp.rk);
   const R cos_t = R(2) * u01<R>(r.x) - R(1);
-  const R sin_t = sqrt_r(rmax0(R(1) - cos_t * cos_t));
+  const R sin_t = M::sqrt0(R(1) - cos_t * cos_t);
   R sp, cp;
-  rsincospi(R(2) * u01<R>(r.y), &sp, &cp);
-  const R rad = sqrt_r(rmax0(R(1) - a0 * a0));
+  M::sincos2pi(u01<R>(r.y), &sp, &cp);
+  const R rad = M::sqrt0(R(1) - a0 * a0);
   const Quat<R> x = qmake<R>(a0, rad * sin_t * cp, rad * sin_t * sp, rad * cos_t);
-  const R invk = R(1) / k;
   *out = qmul(x, qscale(sigma, invk));
   return n;
 }
@@ -215,26 +285,27 @@ __device__ __forceinline__ int heatbath_draw(const Quat<R>& sigma, uint4 ctr, co
 // ---------------------------------------------------------------------------
 // Link store: structure of arrays.  Class c = 2 mu + parity holds the V/2
 // links of direction mu on sites of that parity, ordered by s >> 1.
-// ---------------------------------------------------------------------------
-template <int P> struct Links;
-
 // ld() reads through the read-only path (valid while no thread of the same
 // kernel writes the element); ldc() is a plain coherent load for kernels that
 // write links other blocks read after a grid barrier.
+// ---------------------------------------------------------------------------
+template <int P> struct Links;
+
 template <> struct Links<kF64> {
   double2* p;     // 2 double2 per link
   int64_t vh;     // links per class
-  __device__ __forceinline__ Quat<double> ld(int cls, int64_t i) const {
-    const double2* q = p + 2 * (cls * vh + i);
+  __device__ __forceinline__ const double2* at(int cls, int i) const { return p + 2 * (cls * vh + i); }
+  __device__ __forceinline__ Quat<double> ld(int cls, int i) const {
+    const double2* q = at(cls, i);
     const double2 a = __ldg(q), b = __ldg(q + 1);
     return qmake<double>(a.x, a.y, b.x, b.y);
   }
-  __device__ __forceinline__ Quat<double> ldc(int cls, int64_t i) const {
-    const double2* q = p + 2 * (cls * vh + i);
+  __device__ __forceinline__ Quat<double> ldc(int cls, int i) const {
+    const double2* q = at(cls, i);
     const double2 a = q[0], b = q[1];
     return qmake<double>(a.x, a.y, b.x, b.y);
   }
-  __device__ __forceinline__ void st(int cls, int64_t i, const Quat<double>& v) const {
+  __device__ __forceinline__ void st(int cls, int i, const Quat<double>& v) const {
     double2* q = p + 2 * (cls * vh + i);
     q[0] = make_double2(v.w, v.x);
     q[1] = make_double2(v.y, v.z);
@@ -244,15 +315,15 @@ template <> struct Links<kF64> {
 template <> struct Links<kF32> {
   float4* p;
   int64_t vh;
-  __device__ __forceinline__ Quat<float> ld(int cls, int64_t i) const {
+  __device__ __forceinline__ Quat<float> ld(int cls, int i) const {
     const float4 a = __ldg(p + cls * vh + i);
     return qmake<float>(a.x, a.y, a.z, a.w);
   }
-  __device__ __forceinline__ Quat<float> ldc(int cls, int64_t i) const {
+  __device__ __forceinline__ Quat<float> ldc(int cls, int i) const {
     const float4 a = p[cls * vh + i];
     return qmake<float>(a.x, a.y, a.z, a.w);
   }
-  __device__ __forceinline__ void st(int cls, int64_t i, const Quat<float>& v) const {
+  __device__ __forceinline__ void st(int cls, int i, const Quat<float>& v) const {
     p[cls * vh + i] = make_float4(v.w, v.x, v.y, v.z);
   }
 };
@@ -261,16 +332,15 @@ template <> struct Links<kF32> {
 template <> struct Links<kF16Q> {
   uint2* p;
   int64_t vh;
-  __device__ __forceinline__ Quat<float> ld(int cls, int64_t i) const { return unpack(__ldg(p + cls * vh + i)); }
-  __device__ __forceinline__ Quat<float> ldc(int cls, int64_t i) const { return unpack(p[cls * vh + i]); }
+  __device__ __forceinline__ Quat<float> ld(int cls, int i) const { return unpack(__ldg(p + cls * vh + i)); }
+  __device__ __forceinline__ Quat<float> ldc(int cls, int i) const { return unpack(p[cls * vh + i]); }
   static __device__ __forceinline__ Quat<float> unpack(const uint2 a) {
     const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
     const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
     Quat<float> q = qmake<float>(lo.x, lo.y, hi.x, hi.y);
-    const float inv = rsqrtf(qdot(q, q));
-    return qscale(q, inv);
+    return qscale(q, rsqrtf(qdot(q, q)));
   }
-  __device__ __forceinline__ void st(int cls, int64_t i, const Quat<float>& v) const {
+  __device__ __forceinline__ void st(int cls, int i, const Quat<float>& v) const {
     const __half2 lo = __floats2half2_rn(v.w, v.x);
     const __half2 hi = __floats2half2_rn(v.y, v.z);
     uint2 a;
@@ -279,6 +349,11 @@ template <> struct Links<kF16Q> {
     p[cls * vh + i] = a;
   }
 };
+
+template <int P, bool NC>
+__device__ __forceinline__ Quat<typename Real<P>::T> ldl(const Links<P>& L, int cls, int i) {
+  return NC ? L.ld(cls, i) : L.ldc(cls, i);
+}
 
 // ---------------------------------------------------------------------------
 // Division by a runtime-invariant divisor with one multiply-high (Granlund &
@@ -299,94 +374,170 @@ struct FastDiv {
   }
 };
 
-// Checkerboard geometry of one lattice.
+// Checkerboard geometry of one lattice.  A site's "row" is
+// x1 + n1 (x2 + n2 x3); its half-site index is (x0 >> 1) + n0h * row.
 struct Geom {
   int n[4];         // extents
   int n0h;          // n[0] / 2
   int64_t vh;       // V / 2
+  int st[4];        // row stride of a unit step in direction 1..3 (st[0] unused)
+  int wr[4];        // st[d] * (n[d] - 1): row change of a wrapping step
   FastDiv f_n0h, f_n1, f_n2, f_n0;
 };
 
-// Half-site index of (x0..x3): (x0 >> 1) + n0h (x1 + n1 (x2 + n2 x3)).
-__device__ __forceinline__ int64_t hidx(const Geom& g, int x0, int x1, int x2, int x3) {
-  return (int64_t)(x0 >> 1) + (int64_t)g.n0h * (x1 + g.n[1] * (x2 + g.n[2] * (int64_t)x3));
+// A site: scalar coordinates and its row; only compile-time indices are used.
+struct Site {
+  int x0, x1, x2, x3;
+  int row;
+};
+
+template <int D> __device__ __forceinline__ int& coord(Site& s) {
+  return D == 0 ? s.x0 : D == 1 ? s.x1 : D == 2 ? s.x2 : s.x3;
 }
 
-__device__ __forceinline__ int wrap_inc(int x, int n) { return x + 1 == n ? 0 : x + 1; }
-__device__ __forceinline__ int wrap_dec(int x, int n) { return x == 0 ? n - 1 : x - 1; }
+// s + S * D-hat with periodic boundaries (S = +1 or -1).
+template <int D, int S> __device__ __forceinline__ Site shifted(const Geom& g, Site s) {
+  int& x = coord<D>(s);
+  if (S > 0) {
+    if (x + 1 == g.n[D]) { x = 0; if (D) s.row -= g.wr[D]; }
+    else { x += 1; if (D) s.row += g.st[D]; }
+  } else {
+    if (x == 0) { x = g.n[D] - 1; if (D) s.row += g.wr[D]; }
+    else { x -= 1; if (D) s.row -= g.st[D]; }
+  }
+  return s;
+}
 
-// Coordinates of half-site h on the parity-p sublattice.
-__device__ __forceinline__ void decode_half(const Geom& g, uint32_t h, int p, int x[4]) {
+__device__ __forceinline__ int hidx(const Geom& g, const Site& s) { return (s.x0 >> 1) + g.n0h * s.row; }
+__device__ __forceinline__ uint32_t site_index(const Geom& g, const Site& s) {
+  return (uint32_t)(s.x0 + g.n[0] * s.row);
+}
+__device__ __forceinline__ int parity(const Site& s) { return (s.x0 + s.x1 + s.x2 + s.x3) & 1; }
+
+// Site with half-index h on the parity-p sublattice.
+__device__ __forceinline__ Site site_from_half(const Geom& g, uint32_t h, int p) {
+  Site s;
   const uint32_t row = g.f_n0h.div(h);
   const int xh = (int)(h - row * (uint32_t)g.n0h);
   const uint32_t r2 = g.f_n1.div(row);
-  x[1] = (int)(row - r2 * (uint32_t)g.n[1]);
+  s.x1 = (int)(row - r2 * (uint32_t)g.n[1]);
   const uint32_t r3 = g.f_n2.div(r2);
-  x[2] = (int)(r2 - r3 * (uint32_t)g.n[2]);
-  x[3] = (int)r3;
-  x[0] = 2 * xh + ((x[1] + x[2] + x[3] + p) & 1);
+  s.x2 = (int)(r2 - r3 * (uint32_t)g.n[2]);
+  s.x3 = (int)r3;
+  s.x0 = 2 * xh + ((s.x1 + s.x2 + s.x3 + p) & 1);
+  s.row = (int)row;
+  return s;
 }
 
-// Coordinates of full site s.
-__device__ __forceinline__ void decode_site(const Geom& g, uint32_t s, int x[4]) {
-  const uint32_t r1 = g.f_n0.div(s);
-  x[0] = (int)(s - r1 * (uint32_t)g.n[0]);
-  const uint32_t r2 = g.f_n1.div(r1);
-  x[1] = (int)(r1 - r2 * (uint32_t)g.n[1]);
+// Site with full index s.
+__device__ __forceinline__ Site site_from_index(const Geom& g, uint32_t i) {
+  Site s;
+  const uint32_t row = g.f_n0.div(i);
+  s.x0 = (int)(i - row * (uint32_t)g.n[0]);
+  const uint32_t r2 = g.f_n1.div(row);
+  s.x1 = (int)(row - r2 * (uint32_t)g.n[1]);
   const uint32_t r3 = g.f_n2.div(r2);
-  x[2] = (int)(r2 - r3 * (uint32_t)g.n[2]);
-  x[3] = (int)r3;
+  s.x2 = (int)(r2 - r3 * (uint32_t)g.n[2]);
+  s.x3 = (int)r3;
+  s.row = (int)row;
+  return s;
 }
 
-__device__ __forceinline__ uint32_t site_of(const Geom& g, const int x[4]) {
-  return (uint32_t)(x[0] + g.n[0] * (x[1] + g.n[1] * (x[2] + g.n[2] * x[3])));
+// The two staple terms of Section 2 Eq. 11 for link (x, MU) and one NU != MU:
+// U_nu(x) U_mu(x+nu) U_nu(x+mu)^dagger + U_nu(x-nu)^dagger U_mu(x-nu)
+// U_nu(x-nu+mu).  U_nu(x) and U_nu(x-nu+mu) have the parity p of x; the four
+// singly shifted links have parity 1-p.
+template <int P, int MU, int NU, bool NC>
+__device__ __forceinline__ void staple_term(const Links<P>& L, const Geom& g, const Site& x, int h,
+                                            int h_pmu, int p, Quat<typename Real<P>::T>& s) {
+  using R = typename Real<P>::T;
+  const int q = p ^ 1;
+  const Site xmnu = shifted<NU, -1>(g, x);
+  const int h_pnu = hidx(g, shifted<NU, +1>(g, x));
+  const int h_mnu = hidx(g, xmnu);
+  const int h_mp = hidx(g, shifted<MU, +1>(g, xmnu));
+  const Quat<R> a = ldl<P, NC>(L, 2 * NU + p, h);       // U_nu(x)
+  const Quat<R> b = ldl<P, NC>(L, 2 * MU + q, h_pnu);   // U_mu(x+nu)
+  const Quat<R> c = ldl<P, NC>(L, 2 * NU + q, h_pmu);   // U_nu(x+mu)
+  const Quat<R> d = ldl<P, NC>(L, 2 * NU + q, h_mnu);   // U_nu(x-nu)
+  const Quat<R> e = ldl<P, NC>(L, 2 * MU + q, h_mnu);   // U_mu(x-nu)
+  const Quat<R> f = ldl<P, NC>(L, 2 * NU + p, h_mp);    // U_nu(x-nu+mu)
+  qacc_mul_nd(s, qmul(a, b), c);
+  qacc_mul(s, qmul_dn(d, e), f);
 }
 
-// Half-site index of x shifted by +-1 along d (periodic).
-__device__ __forceinline__ int64_t hidx_shift(const Geom& g, const int x[4], int d, int step) {
-  int y[4] = {x[0], x[1], x[2], x[3]};
-  y[d] = step > 0 ? wrap_inc(y[d], g.n[d]) : wrap_dec(y[d], g.n[d]);
-  return hidx(g, y[0], y[1], y[2], y[3]);
+// The six links of staple_term, loaded (no arithmetic).
+template <class R> struct StapleLinks { Quat<R> a, b, c, d, e, f; };
+
+template <int P, int MU, int NU, bool NC>
+__device__ __forceinline__ void staple_load(const Links<P>& L, const Geom& g, const Site& x, int h, int h_pmu,
+                                            int p, StapleLinks<typename Real<P>::T>& t) {
+  const int q = p ^ 1;
+  const Site xmnu = shifted<NU, -1>(g, x);
+  const int h_pnu = hidx(g, shifted<NU, +1>(g, x));
+  const int h_mnu = hidx(g, xmnu);
+  const int h_mp = hidx(g, shifted<MU, +1>(g, xmnu));
+  t.a = ldl<P, NC>(L, 2 * NU + p, h);
+  t.b = ldl<P, NC>(L, 2 * MU + q, h_pnu);
+  t.c = ldl<P, NC>(L, 2 * NU + q, h_pmu);
+  t.d = ldl<P, NC>(L, 2 * NU + q, h_mnu);
+  t.e = ldl<P, NC>(L, 2 * MU + q, h_mnu);
+  t.f = ldl<P, NC>(L, 2 * NU + p, h_mp);
 }
 
-// Half-site index of x - nu + mu.
-__device__ __forceinline__ int64_t hidx_mp(const Geom& g, const int x[4], int nu, int mu) {
-  int y[4] = {x[0], x[1], x[2], x[3]};
-  y[nu] = wrap_dec(y[nu], g.n[nu]);
-  y[mu] = wrap_inc(y[mu], g.n[mu]);
-  return hidx(g, y[0], y[1], y[2], y[3]);
+template <class R> __device__ __forceinline__ void staple_add(const StapleLinks<R>& t, Quat<R>& s) {
+  qacc_mul_nd(s, qmul(t.a, t.b), t.c);
+  qacc_mul(s, qmul_dn(t.d, t.e), t.f);
 }
 
-// Staple sum of Section 2 Eq. 11 for link (x, mu), x of parity p with
-// half-index h: for nu != mu, U_nu(x) U_mu(x+nu) U_nu(x+mu)^dagger +
-// U_nu(x-nu)^dagger U_mu(x-nu) U_nu(x-nu+mu).  Classes: U_nu(x) and
-// U_nu(x-nu+mu) have parity p; the four shifted links have parity 1-p.
-// `nmask` selects which nu contribute (all nu != mu for the heat bath; the
-// spatial ones for APE).
-template <int P, bool NC = true>
+#ifndef SU2_STAPLE_LOADS_FIRST
+#define SU2_STAPLE_LOADS_FIRST 0
+#endif
+
+// Staple sum for link (x, MU) over the directions NU != MU selected by NMASK
+// (0xF: all, the heat bath; 0x7: the spatial ones, APE smearing).  With
+// SU2_STAPLE_LOADS_FIRST the loads of all directions are issued before any
+// product, so a warp has every load of the update in flight at once.
+template <int P, int MU, int NMASK, bool NC>
 __device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P>& L, const Geom& g,
-                                                           const int x[4], int64_t h, int mu,
-                                                           int p, int nmask) {
+                                                           const Site& x, int h, int p) {
   using R = typename Real<P>::T;
   Quat<R> s = qmake<R>(0, 0, 0, 0);
-  const int q = p ^ 1;
-  const int64_t h_pmu = hidx_shift(g, x, mu, +1);
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == mu || !((nmask >> nu) & 1)) continue;
-    const int64_t h_pnu = hidx_shift(g, x, nu, +1);
-    const int64_t h_mnu = hidx_shift(g, x, nu, -1);
-    const int64_t h_mp = hidx_mp(g, x, nu, mu);
-    const Quat<R> a = NC ? L.ld(2 * nu + p, h) : L.ldc(2 * nu + p, h);              // U_nu(x)
-    const Quat<R> b = NC ? L.ld(2 * mu + q, h_pnu) : L.ldc(2 * mu + q, h_pnu);      // U_mu(x+nu)
-    const Quat<R> c = NC ? L.ld(2 * nu + q, h_pmu) : L.ldc(2 * nu + q, h_pmu);      // U_nu(x+mu)
-    const Quat<R> d = NC ? L.ld(2 * nu + q, h_mnu) : L.ldc(2 * nu + q, h_mnu);      // U_nu(x-nu)
-    const Quat<R> e = NC ? L.ld(2 * mu + q, h_mnu) : L.ldc(2 * mu + q, h_mnu);      // U_mu(x-nu)
-    const Quat<R> f = NC ? L.ld(2 * nu + p, h_mp) : L.ldc(2 * nu + p, h_mp);        // U_nu(x-nu+mu)
-    qacc(s, qmul_nd(qmul(a, b), c));
-    qacc(s, qmul(qmul_dn(d, e), f));
+  const int h_pmu = hidx(g, shifted<MU, +1>(g, x));
+  if (SU2_STAPLE_LOADS_FIRST) {
+    // the three directions NU != MU (for NMASK 0x7 and MU < 3 only two)
+    constexpr int N0 = MU == 0 ? 1 : 0;
+    constexpr int N1 = MU <= 1 ? 2 : 1;
+    constexpr int N2 = MU <= 2 ? 3 : 2;
+    StapleLinks<R> t0, t1, t2;
+    if (NMASK & (1 << N0)) staple_load<P, MU, N0, NC>(L, g, x, h, h_pmu, p, t0);
+    if (NMASK & (1 << N1)) staple_load<P, MU, N1, NC>(L, g, x, h, h_pmu, p, t1);
+    if (NMASK & (1 << N2)) staple_load<P, MU, N2, NC>(L, g, x, h, h_pmu, p, t2);
+    if (NMASK & (1 << N0)) staple_add(t0, s);
+    if (NMASK & (1 << N1)) staple_add(t1, s);
+    if (NMASK & (1 << N2)) staple_add(t2, s);
+    return s;
   }
+  if (MU != 0 && (NMASK & 1)) staple_term<P, MU, 0, NC>(L, g, x, h, h_pmu, p, s);
+  if (MU != 1 && (NMASK & 2)) staple_term<P, MU, 1, NC>(L, g, x, h, h_pmu, p, s);
+  if (MU != 2 && (NMASK & 4)) staple_term<P, MU, 2, NC>(L, g, x, h, h_pmu, p, s);
+  if (MU != 3 && (NMASK & 8)) staple_term<P, MU, 3, NC>(L, g, x, h, h_pmu, p, s);
   return s;
+}
+
+// One heat-bath update of link (x, MU): staple, draw, store (a capped link
+// is neither read nor written).  Returns the draw's trial count.
+template <int P, int MU, bool NC>
+__device__ __forceinline__ int heatbath_site(const Links<P>& L, const Geom& g, const Site& x, int h,
+                                             int p, uint32_t sweep, const HBParams& hp,
+                                             typename Real<P>::T beta) {
+  using R = typename Real<P>::T;
+  const Quat<R> sig = staple<P, MU, 0xF, NC>(L, g, x, h, p);
+  Quat<R> nl;
+  const uint4 ctr = make_uint4(site_index(g, x), (uint32_t)MU | hp.lattice_tag, sweep, 0u);
+  const int n = heatbath_draw<R>(sig, ctr, hp, beta, &nl);
+  if (n != 0) L.st(2 * MU + p, h, nl);
+  return n;
 }
 
 }  // namespace su2

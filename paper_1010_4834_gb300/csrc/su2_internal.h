@@ -60,4 +60,15 @@ cudaError_t launch_from_canonical(const LatticeView& v, const double* canon, int
                                   int64_t ns, cudaStream_t st);
 cudaError_t launch_add_u32(uint32_t* p, uint32_t v, cudaStream_t st);
 
+// Process-wide count of kernels this library launched (graph replays add
+// their kernel-node count through count_launches).
+void count_launches(uint64_t n);
+uint64_t launches_total();
+// While alive on a thread, launches made by that thread (stream capture) are
+// not counted; the replays of the captured graph are.
+struct CaptureScope {
+  CaptureScope();
+  ~CaptureScope();
+};
+
 }  // namespace su2

@@ -4,12 +4,13 @@
 // the canonical-layout conversions.  Paper: Cardoso & Bicudo,
 // arXiv:1010.4834 (Sections 2 and 4).
 //
-// None of these work is a dense contraction (2x2 SU(2) products in
+// None of this work is a dense contraction (2x2 SU(2) products in
 // registers), so everything runs on the FP32/FP64 pipes; the sweep is bound
 // by HBM traffic and ALU issue.  Reductions are fused into the measurement
 // kernels: per-thread compensated sums, warp shuffles, one partial per block
 // and a last-block finisher that adds the partials in a fixed order, so a
 // result is reproducible run to run.
+#include <atomic>
 #include <cfloat>
 
 #include "su2_internal.h"
@@ -17,6 +18,15 @@
 namespace su2 {
 
 constexpr int kThreads = 256;
+
+static std::atomic<uint64_t> g_launches{0};
+static thread_local int g_capturing = 0;
+void count_launches(uint64_t n) {
+  if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+CaptureScope::CaptureScope() { ++g_capturing; }
+CaptureScope::~CaptureScope() { --g_capturing; }
 
 // ---------------------------------------------------------------------------
 // Device info and launch shapes
@@ -41,6 +51,11 @@ Geom make_geom(const int n[4]) {
   for (int i = 0; i < 4; ++i) g.n[i] = n[i];
   g.n0h = n[0] / 2;
   g.vh = (int64_t)n[0] * n[1] * n[2] * n[3] / 2;
+  g.st[0] = 0;
+  g.st[1] = 1;
+  g.st[2] = n[1];
+  g.st[3] = n[1] * n[2];
+  for (int d = 0; d < 4; ++d) g.wr[d] = d ? g.st[d] * (n[d] - 1) : 0;
   g.f_n0h = FastDiv((uint32_t)g.n0h);
   g.f_n1 = FastDiv((uint32_t)n[1]);
   g.f_n2 = FastDiv((uint32_t)n[2]);
@@ -52,8 +67,8 @@ size_t scratch_bytes() {
   return kScratchPartials * sizeof(double) + 256 + kScratchOut * sizeof(double) + 256;
 }
 
-// Blocks for `work` items with a grid-stride loop: enough to fill every SM
-// `waves` times over at the kernel's occupancy, never more than needed.
+// Blocks for `work` items with a grid-stride loop: every SM filled to the
+// kernel's occupancy, never more blocks than items need.
 template <class K>
 static int grid_for(K kernel, int64_t work, int smem = 0) {
   int per_sm = 1;
@@ -136,29 +151,65 @@ __device__ __forceinline__ bool block_partial(double (&v)[NV], double* partials,
   return last;
 }
 
-// In the last block: tot[k] = sum over blocks of partials[b*NV + k], summed in
-// a fixed order (strided per thread, then thread order), compensated.
+// Neumaier pairs combine as (a.s + b.s with its rounding error) + a.c + b.c.
+__device__ __forceinline__ KSum ksum_combine(KSum a, const KSum& b) {
+  a.add(b.s);
+  a.c += b.c;
+  return a;
+}
+
+// Fixed-order tree over the lanes of a warp; lane 0 ends with the total.
+__device__ __forceinline__ KSum warp_ksum(KSum a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    KSum o;
+    o.s = __shfl_xor_sync(0xffffffffu, a.s, off);
+    o.c = __shfl_xor_sync(0xffffffffu, a.c, off);
+    a = ksum_combine(a, o);
+  }
+  return a;
+}
+
+// In the last block: tot[k] = sum over blocks of partials[b*NV + k].  Every
+// thread adds a strided subset (compensated), then a fixed-order tree over
+// lanes and warps combines them, so the result does not depend on timing and
+// no thread runs a long serial FP64 chain.
 template <int NV>
 __device__ __forceinline__ void final_sum(const double* partials, int nblocks, double (&tot)[NV]) {
-  __shared__ double ss[kThreads][NV], sc[kThreads][NV];
+  __shared__ double ss[kThreads / 32][NV], sc[kThreads / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     KSum a;
     for (int b = threadIdx.x; b < nblocks; b += kThreads) a.add(__ldcg(partials + (size_t)b * NV + k));
-    ss[threadIdx.x][k] = a.s;
-    sc[threadIdx.x][k] = a.c;
+    a = warp_ksum(a);
+    if (lane == 0) {
+      ss[warp][k] = a.s;
+      sc[warp][k] = a.c;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       KSum a;
-      double comp = 0.0;
-      for (int t = 0; t < kThreads; ++t) { a.add(ss[t][k]); comp += sc[t][k]; }
-      tot[k] = a.value() + comp;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        KSum o;
+        o.s = ss[w][k];
+        o.c = sc[w][k];
+        a = ksum_combine(a, o);
+      }
+      tot[k] = a.value();
     }
   }
 }
+
+// Occupancy targets (blocks of 256 per SM) for the register-heavy kernels.
+#ifndef SU2_HB_MINB
+#define SU2_HB_MINB 4
+#endif
+template <int P> struct Occ { static constexpr int hb = SU2_HB_MINB; };
+template <> struct Occ<kF64> { static constexpr int hb = 2; };
 
 // ---------------------------------------------------------------------------
 // Start configurations (Section 4 kernel list: cold start U = 1, hot start a
@@ -166,7 +217,8 @@ __device__ __forceinline__ void final_sum(const double* partials, int nblocks, d
 // 0xFFFFFFFF).  One thread per (site, direction).
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_init(Links<P> L, Geom g, int start, PhiloxKey key,
+__global__ void __launch_bounds__(kThreads) k_init(Links<P> L, Geom g, int start,
+                                                   const __grid_constant__ RoundKeys rk,
                                                    uint32_t lattice_tag) {
   using R = typename Real<P>::T;
   const int64_t V = 2 * g.vh;
@@ -174,38 +226,29 @@ __global__ void __launch_bounds__(kThreads) k_init(Links<P> L, Geom g, int start
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < 4 * V; w += stride) {
     const int mu = (int)(w / V);
     const uint32_t s = (uint32_t)(w - (int64_t)mu * V);
-    int x[4];
-    decode_site(g, s, x);
-    const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const Site x = site_from_index(g, s);
     Quat<R> q = qone<R>();
-    if (start) q = haar_from<R>(philox4x32_10(make_uint4(s, (uint32_t)mu | lattice_tag, 0xFFFFFFFFu, 0u), key));
-    L.st(2 * mu + p, s >> 1, q);
+    if (start) q = haar_from<R>(philox(make_uint4(s, (uint32_t)mu | lattice_tag, 0xFFFFFFFFu, 0u), rk));
+    L.st(2 * mu + parity(x), hidx(g, x), q);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Heat-bath substep (Section 2 Eqs. 5-9, 11; Section 4 checkerboard): one
-// thread per link of direction mu on the parity-p sublattice.  A capped link
-// (all trials rejected) is neither read nor written.
+// thread per link of direction MU on the parity-p sublattice.
 // ---------------------------------------------------------------------------
-template <int P>
-__global__ void __launch_bounds__(kThreads) k_heatbath(Links<P> L, Geom g, int mu, int p,
-                                                       const uint32_t* sweep_base,
-                                                       uint32_t sweep_off, HBParams hp,
-                                                       unsigned long long* stats) {
+template <int P, int MU>
+__global__ void __launch_bounds__(kThreads, Occ<P>::hb)
+    k_heatbath(Links<P> L, Geom g, int p, const uint32_t* sweep_base, uint32_t sweep_off,
+               const __grid_constant__ HBParams hp, unsigned long long* stats) {
   using R = typename Real<P>::T;
   const R beta = (R)hp.beta;
   const uint32_t sweep = (sweep_base ? *sweep_base : 0u) + sweep_off;
-  const uint32_t tag = (uint32_t)mu | hp.lattice_tag;
   unsigned int trials = 0, capped = 0, haar = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < g.vh; h += stride) {
-    int x[4];
-    decode_half(g, (uint32_t)h, p, x);
-    const Quat<R> sig = staple<P>(L, g, x, h, mu, p, 0xF);
-    Quat<R> nl;
-    const int n = heatbath_draw<R>(sig, make_uint4(site_of(g, x), tag, sweep, 0u), hp, beta, &nl);
-    if (n != 0) L.st(2 * mu + p, h, nl);
+  const int stride = gridDim.x * blockDim.x;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.vh; h += stride) {
+    const Site x = site_from_half(g, (uint32_t)h, p);
+    const int n = heatbath_site<P, MU, true>(L, g, x, h, p, sweep, hp, beta);
     if (stats) {
       trials += n > 0 ? (unsigned)n : (n == 0 ? (unsigned)hp.max_tries : 0u);
       capped += n == 0;
@@ -228,19 +271,19 @@ __global__ void __launch_bounds__(kThreads) k_heatbath(Links<P> L, Geom g, int m
 // Over-relaxation substep (Section 2, Eq. 10 with W = Sigma/|Sigma| for the
 // orientation of Eq. 11): U' = W U^dagger W keeps Tr(U Sigma^dagger).
 // ---------------------------------------------------------------------------
-template <int P>
-__global__ void __launch_bounds__(kThreads) k_overrelax(Links<P> L, Geom g, int mu, int p) {
+template <int P, int MU>
+__global__ void __launch_bounds__(kThreads, Occ<P>::hb) k_overrelax(Links<P> L, Geom g, int p) {
   using R = typename Real<P>::T;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < g.vh; h += stride) {
-    int x[4];
-    decode_half(g, (uint32_t)h, p, x);
-    const Quat<R> sig = staple<P>(L, g, x, h, mu, p, 0xF);
+  using M = Math<R>;
+  const int stride = gridDim.x * blockDim.x;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.vh; h += stride) {
+    const Site x = site_from_half(g, (uint32_t)h, p);
+    const Quat<R> sig = staple<P, MU, 0xF, true>(L, g, x, h, p);
     const R k2 = qdot(sig, sig);
-    if (!(k2 >= R(P == kF64 ? 1e-300 : 1e-30))) continue;
-    const Quat<R> w = qscale(sig, R(1) / sqrt_r(k2));
-    const Quat<R> u = L.ld(2 * mu + p, h);
-    L.st(2 * mu + p, h, qmul(qmul_nd(w, u), w));
+    if (!(k2 >= M::kTiny)) continue;
+    const Quat<R> w = qscale(sig, M::rsqrt(k2));
+    const Quat<R> u = L.ld(2 * MU + p, h);
+    L.st(2 * MU + p, h, qmul(qmul_nd(w, u), w));
   }
 }
 
@@ -251,35 +294,35 @@ __global__ void __launch_bounds__(kThreads) k_overrelax(Links<P> L, Geom g, int 
 // out[0] all, out[1] spatial, out[2] space-time means.
 // ---------------------------------------------------------------------------
 template <int P>
+__device__ __forceinline__ typename Real<P>::T plaq(const Links<P>& L, int q, const Quat<typename Real<P>::T>& umu,
+                                                   const Quat<typename Real<P>::T>& unu, int mu, int nu,
+                                                   int h_pmu, int h_pnu) {
+  using R = typename Real<P>::T;
+  const Quat<R> a = qmul(umu, L.ld(2 * nu + q, h_pmu));
+  const Quat<R> b = qmul(unu, L.ld(2 * mu + q, h_pnu));
+  return qdot(a, b);
+}
+
+template <int P>
 __global__ void __launch_bounds__(kThreads) k_plaquette(Links<P> L, Geom g, double* partials,
                                                         unsigned int* counter, double* out) {
   using R = typename Real<P>::T;
   Acc<R> sp, tm;
-  const int64_t V = 2 * g.vh;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
-    int x[4];
-    decode_site(g, (uint32_t)s, x);
-    const int p = (x[0] + x[1] + x[2] + x[3]) & 1, q = p ^ 1;
-    const int64_t h = s >> 1;
-    Quat<R> u[4];
-    int64_t hp[4];
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      u[mu] = L.ld(2 * mu + p, h);
-      hp[mu] = hidx_shift(g, x, mu, +1);
-    }
-    R ssum = 0, tsum = 0;
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-#pragma unroll
-      for (int nu = mu + 1; nu < 4; ++nu) {
-        const Quat<R> a = qmul(u[mu], L.ld(2 * nu + q, hp[mu]));
-        const Quat<R> b = qmul(u[nu], L.ld(2 * mu + q, hp[nu]));
-        const R v = qdot(a, b);
-        if (nu == 3) tsum += v; else ssum += v;
-      }
-    }
+  const int V = (int)(2 * g.vh);
+  const int stride = gridDim.x * blockDim.x;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
+    const Site x = site_from_index(g, (uint32_t)s);
+    const int p = parity(x), q = p ^ 1;
+    const int h = s >> 1;
+    const Quat<R> u0 = L.ld(0 + p, h), u1 = L.ld(2 + p, h), u2 = L.ld(4 + p, h), u3 = L.ld(6 + p, h);
+    const int h0 = hidx(g, shifted<0, +1>(g, x));
+    const int h1 = hidx(g, shifted<1, +1>(g, x));
+    const int h2 = hidx(g, shifted<2, +1>(g, x));
+    const int h3 = hidx(g, shifted<3, +1>(g, x));
+    const R ssum = plaq<P>(L, q, u0, u1, 0, 1, h0, h1) + plaq<P>(L, q, u0, u2, 0, 2, h0, h2) +
+                   plaq<P>(L, q, u1, u2, 1, 2, h1, h2);
+    const R tsum = plaq<P>(L, q, u0, u3, 0, 3, h0, h3) + plaq<P>(L, q, u1, u3, 1, 3, h1, h3) +
+                   plaq<P>(L, q, u2, u3, 2, 3, h2, h3);
     sp.add(ssum);
     tm.add(tsum);
   }
@@ -300,23 +343,32 @@ __global__ void __launch_bounds__(kThreads) k_plaquette(Links<P> L, Geom g, doub
 // ---------------------------------------------------------------------------
 // Polyakov loop (Section 2, Eqs. 14-15): per spatial site the product of the
 // time links in increasing t; mean of (1/2) Tr over the spatial sites.  Site
-// s = xs + Nsigma t has half-index (xs >> 1) + (Nsigma/2) t.
+// s = xs + Nsigma t has half-index (xs >> 1) + (Nsigma/2) t.  The loads of a
+// chunk of 8 links are issued before the products that consume them.
 // ---------------------------------------------------------------------------
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_polyakov(Links<P> L, Geom g, double* partials,
                                                        unsigned int* counter, double* out) {
   using R = typename Real<P>::T;
   Acc<R> acc;
-  const int64_t nsig = (int64_t)g.n[0] * g.n[1] * g.n[2];
-  const int64_t nsig_h = nsig / 2;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t xs = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; xs < nsig; xs += stride) {
-    int x[4];
-    decode_site(g, (uint32_t)xs, x);
-    const int px = (x[0] + x[1] + x[2]) & 1;
-    const int64_t hh = xs >> 1;
-    Quat<R> pr = L.ld(6 + px, hh);
-    for (int t = 1; t < g.n[3]; ++t) pr = qmul(pr, L.ld(6 + ((px + t) & 1), hh + nsig_h * t));
+  const int nsig = g.n[0] * g.n[1] * g.n[2];
+  const int nsig_h = nsig / 2;
+  const int nt = g.n[3];
+  const int stride = gridDim.x * blockDim.x;
+  for (int xs = blockIdx.x * blockDim.x + threadIdx.x; xs < nsig; xs += stride) {
+    const Site x = site_from_index(g, (uint32_t)xs);
+    const int px = parity(x);
+    const int hh = xs >> 1;
+    Quat<R> pr = qone<R>();
+    int t = 0;
+    for (; t + 8 <= nt; t += 8) {
+      Quat<R> u[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) u[j] = L.ld(6 + ((px + t + j) & 1), hh + nsig_h * (t + j));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) pr = qmul(pr, u[j]);
+    }
+    for (; t < nt; ++t) pr = qmul(pr, L.ld(6 + ((px + t) & 1), hh + nsig_h * t));
     acc.add(pr.w);
   }
   double v[1] = {acc.value()};
@@ -335,29 +387,36 @@ __global__ void __launch_bounds__(kThreads) k_polyakov(Links<P> L, Geom g, doubl
 // P[(1-alpha) U + (alpha/4) (four spatial staples)], P = normalisation; a sum
 // with vanishing norm keeps U.  blockIdx.y = mu in 0..2.
 // ---------------------------------------------------------------------------
-template <int P>
-__global__ void __launch_bounds__(kThreads) k_ape(Links<P> src, Links<P> dst, Geom g,
-                                                  double alpha_d) {
+template <int P, int MU>
+__device__ __forceinline__ void ape_site(const Links<P>& src, const Links<P>& dst, const Geom& g, int s,
+                                         typename Real<P>::T c0, typename Real<P>::T c1) {
   using R = typename Real<P>::T;
-  const int mu = blockIdx.y;
+  using M = Math<R>;
+  const Site x = site_from_index(g, (uint32_t)s);
+  const int p = parity(x);
+  const int h = s >> 1;
+  const Quat<R> sig = staple<P, MU, 0x7, true>(src, g, x, h, p);
+  const Quat<R> u = src.ld(2 * MU + p, h);
+  const Quat<R> q = qmake<R>(c0 * u.w + c1 * sig.w, c0 * u.x + c1 * sig.x, c0 * u.y + c1 * sig.y,
+                             c0 * u.z + c1 * sig.z);
+  const R n2 = qdot(q, q);
+  dst.st(2 * MU + p, h, n2 >= M::kTiny ? qscale(q, M::rsqrt(n2)) : u);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, Occ<P>::hb) k_ape(Links<P> src, Links<P> dst, Geom g,
+                                                              double alpha_d) {
+  using R = typename Real<P>::T;
   const R alpha = (R)alpha_d;
   const R c0 = R(1) - alpha, c1 = R(0.25) * alpha;
-  const int64_t V = 2 * g.vh;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
-    int x[4];
-    decode_site(g, (uint32_t)s, x);
-    const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
-    const int64_t h = s >> 1;
-    const Quat<R> sig = staple<P>(src, g, x, h, mu, p, 0x7);
-    const Quat<R> u = src.ld(2 * mu + p, h);
-    const Quat<R> q = qmake<R>(c0 * u.w + c1 * sig.w, c0 * u.x + c1 * sig.x, c0 * u.y + c1 * sig.y,
-                               c0 * u.z + c1 * sig.z);
-    const R n2 = qdot(q, q);
-    if (n2 >= R(P == kF64 ? 1e-300 : 1e-30))
-      dst.st(2 * mu + p, h, qscale(q, R(1) / sqrt_r(n2)));
-    else
-      dst.st(2 * mu + p, h, u);
+  const int V = (int)(2 * g.vh);
+  const int stride = gridDim.x * blockDim.x;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
+    switch (blockIdx.y) {
+      case 0: ape_site<P, 0>(src, dst, g, s, c0, c1); break;
+      case 1: ape_site<P, 1>(src, dst, g, s, c0, c1); break;
+      default: ape_site<P, 2>(src, dst, g, s, c0, c1); break;
+    }
   }
 }
 
@@ -367,7 +426,7 @@ __global__ void __launch_bounds__(kThreads) k_copy_spatial(Links<P> src, Links<P
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int cls = (int)(i / src.vh);
-    const int64_t j = i - cls * src.vh;
+    const int j = (int)(i - cls * src.vh);
     dst.st(cls, j, src.ld(cls, j));
   }
 }
@@ -375,105 +434,322 @@ __global__ void __launch_bounds__(kThreads) k_copy_spatial(Links<P> src, Links<P
 // ---------------------------------------------------------------------------
 // Wilson loops (Section 2, Eq. 18), (1/2) Tr[S_R(x) T_T(x+R mu) S_R(x+T t)^dag
 // T_T(x)^dag] = (A B) . (D C) with A = S_R(x), B = T_T(x+R mu), C = S_R(x+T t),
-// D = T_T(x).  A thread owns one (site, spatial mu) and a chunk of TC values
+// D = T_T(x).  A thread owns one (site, spatial MU) and a chunk of TC values
 // of T; it walks R = 1..rmax extending A and the TC lines C by one link each,
 // rebuilds the time line B at x + R mu, and adds the TC loop values into the
-// block's shared accumulators (warp sums first).  blockIdx.y = 3 chunk + mu.
+// block's shared accumulators (one transposing warp reduction per R).
+// blockIdx.y = 3 chunk + mu.  Per-block sums go to `partials`; a second
+// kernel adds them per (R, T) in a fixed order.
 // ---------------------------------------------------------------------------
-template <int P>
-__device__ __forceinline__ Quat<typename Real<P>::T> ld_at(const Links<P>& L, const Geom& g,
-                                                          const int y[4], int dir) {
-  const int par = (y[0] + y[1] + y[2] + y[3]) & 1;
-  return L.ld(2 * dir + par, hidx(g, y[0], y[1], y[2], y[3]));
+constexpr int kWilsonMaxR = 32;
+constexpr int kWilsonThreads = 128;
+
+// Walker along the time direction in half-site index space: one step adds
+// the half-index stride of a time slice (wrapping at the last slice) and
+// flips the parity.
+struct TWalk {
+  int h, par, x3;
+  __device__ __forceinline__ void init(const Geom& g, const Site& y) {
+    h = hidx(g, y);
+    par = parity(y);
+    x3 = y.x3;
+  }
+  __device__ __forceinline__ void step(int nt, int hts, int hwrap) {
+    if (x3 + 1 == nt) { x3 = 0; h -= hwrap; } else { ++x3; h += hts; }
+    par ^= 1;
+  }
+};
+
+template <int P, int TC, int MU>
+__device__ __forceinline__ void wilson_site(const Links<P>& Ls, const Links<P>& Lt, const Geom& g, int s,
+                                            bool valid, int rmax, int t0, int nT, double* acc) {
+  using R = typename Real<P>::T;
+  static_assert(TC == 4 || TC == 8 || TC == 16, "T chunk must be 4, 8 or 16");
+  const int lane = threadIdx.x & 31;
+  const int nt = g.n[3];
+  const int hts = g.n0h * g.st[3];
+  const int hwrap = hts * (nt - 1);
+  const Site x = site_from_index(g, (uint32_t)s);
+  Quat<R> D[TC], C[TC];
+  {
+    TWalk w;
+    w.init(g, x);
+    Quat<R> pr = qone<R>();
+    for (int t = 0; t < t0; ++t) { pr = qmul(pr, Lt.ld(6 + w.par, w.h)); w.step(nt, hts, hwrap); }
+#pragma unroll
+    for (int j = 0; j < TC; ++j) {
+      if (j < nT) { pr = qmul(pr, Lt.ld(6 + w.par, w.h)); w.step(nt, hts, hwrap); }
+      D[j] = pr;
+      C[j] = qone<R>();
+    }
+  }
+  Quat<R> A = qone<R>();
+  Site xr = x;  // x + (r-1) mu at the top of iteration r
+  Site zt = x;  // x + (r-1) mu + (t0 + 1) t
+  for (int t = 0; t <= t0; ++t) zt = shifted<3, +1>(g, zt);
+  for (int r = 1; r <= rmax; ++r) {
+    A = qmul(A, Ls.ld(2 * MU + parity(xr), hidx(g, xr)));
+    {
+      TWalk z;
+      z.init(g, zt);
+#pragma unroll
+      for (int j = 0; j < TC; ++j) {
+        if (j < nT) { C[j] = qmul(C[j], Ls.ld(2 * MU + z.par, z.h)); z.step(nt, hts, hwrap); }
+      }
+    }
+    xr = shifted<MU, +1>(g, xr);
+    zt = shifted<MU, +1>(g, zt);
+    TWalk w;
+    w.init(g, xr);
+    Quat<R> b = qone<R>();
+    for (int t = 0; t < t0; ++t) { b = qmul(b, Lt.ld(6 + w.par, w.h)); w.step(nt, hts, hwrap); }
+    R val[TC];
+#pragma unroll
+    for (int j = 0; j < TC; ++j) {
+      val[j] = R(0);
+      if (j < nT) {
+        b = qmul(b, Lt.ld(6 + w.par, w.h));
+        w.step(nt, hts, hwrap);
+        if (valid) val[j] = qdot(qmul(A, b), qmul(D[j], C[j]));
+      }
+    }
+    // Sum the TC values over the warp by a transposing butterfly: each of the
+    // first log2(TC) stages trades half of a lane's values with its partner,
+    // halving the count; the remaining stages finish the sum.  Afterwards the
+    // lanes of each group of 32/TC hold the total of one value j = lo.
+    int nv = TC;
+    int lo = 0;  // this lane's values are j = lo .. lo + nv - 1
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+      if (nv > 1) {
+        const bool upper = (lane & off) != 0;
+        const int half = nv / 2;
+#pragma unroll
+        for (int k = 0; k < TC / 2; ++k) {
+          if (k < half) {
+            const R send = upper ? val[k] : val[k + half];
+            const R keep = upper ? val[k + half] : val[k];
+            val[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+          }
+        }
+        if (upper) lo += half;
+        nv = half;
+      } else {
+        val[0] += __shfl_xor_sync(0xffffffffu, val[0], off);
+      }
+    }
+    if ((lane & (32 / TC - 1)) == 0 && lo < nT) atomicAdd(&acc[(r - 1) * TC + lo], (double)val[0]);
+  }
 }
 
-constexpr int kWilsonMaxR = 32;
-
 template <int P, int TC>
-__global__ void __launch_bounds__(kThreads) k_wilson(Links<P> Ls, Links<P> Lt, Geom g, int rmax,
-                                                     int tmax, double* partials,
-                                                     unsigned int* counter, double* out) {
-  using R = typename Real<P>::T;
+__global__ void __launch_bounds__(kWilsonThreads) k_wilson(Links<P> Ls, Links<P> Lt, Geom g, int rmax,
+                                                           int tmax, double* partials) {
   __shared__ double acc[kWilsonMaxR * TC];
-  __shared__ bool last;
   const int mu = blockIdx.y % 3;
   const int chunk = blockIdx.y / 3;
   const int t0 = chunk * TC;
   const int nT = min(TC, tmax - t0);
-  const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < kWilsonMaxR * TC; i += kThreads) acc[i] = 0.0;
+  for (int i = threadIdx.x; i < kWilsonMaxR * TC; i += blockDim.x) acc[i] = 0.0;
   __syncthreads();
-  const int64_t V = 2 * g.vh;
-  const int nt = g.n[3];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < V; base += stride) {
-    const int64_t s = base + threadIdx.x;
+  const int V = (int)(2 * g.vh);
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < V; base += stride) {
+    const int s = base + threadIdx.x;
     const bool valid = s < V;
-    int x[4];
-    decode_site(g, (uint32_t)(valid ? s : 0), x);
-    Quat<R> D[TC], C[TC];
-    {
-      int y[4] = {x[0], x[1], x[2], x[3]};
-      Quat<R> pr = qone<R>();
-      for (int t = 0; t < t0; ++t) { pr = qmul(pr, ld_at(Lt, g, y, 3)); y[3] = wrap_inc(y[3], nt); }
-#pragma unroll
-      for (int j = 0; j < TC; ++j) {
-        if (j < nT) { pr = qmul(pr, ld_at(Lt, g, y, 3)); y[3] = wrap_inc(y[3], nt); }
-        D[j] = pr;
-        C[j] = qone<R>();
-      }
-    }
-    Quat<R> A = qone<R>();
-    int xr[4] = {x[0], x[1], x[2], x[3]};
-    for (int r = 1; r <= rmax; ++r) {
-      A = qmul(A, ld_at(Ls, g, xr, mu));
-      {
-        int z[4] = {xr[0], xr[1], xr[2], (xr[3] + t0 + 1) % nt};
-#pragma unroll
-        for (int j = 0; j < TC; ++j) {
-          if (j < nT) { C[j] = qmul(C[j], ld_at(Ls, g, z, mu)); z[3] = wrap_inc(z[3], nt); }
-        }
-      }
-      xr[mu] = wrap_inc(xr[mu], g.n[mu]);
-      int w[4] = {xr[0], xr[1], xr[2], xr[3]};
-      Quat<R> b = qone<R>();
-      for (int t = 0; t < t0; ++t) { b = qmul(b, ld_at(Lt, g, w, 3)); w[3] = wrap_inc(w[3], nt); }
-#pragma unroll
-      for (int j = 0; j < TC; ++j) {
-        if (j < nT) {
-          b = qmul(b, ld_at(Lt, g, w, 3));
-          w[3] = wrap_inc(w[3], nt);
-          R val = valid ? qdot(qmul(A, b), qmul(D[j], C[j])) : R(0);
-          val = warp_sum(val);
-          if (lane == 0) atomicAdd(&acc[(r - 1) * TC + j], (double)val);
-        }
-      }
-    }
+    const int sv = valid ? s : 0;
+    if (mu == 0) wilson_site<P, TC, 0>(Ls, Lt, g, sv, valid, rmax, t0, nT, acc);
+    else if (mu == 1) wilson_site<P, TC, 1>(Ls, Lt, g, sv, valid, rmax, t0, nT, acc);
+    else wilson_site<P, TC, 2>(Ls, Lt, g, sv, valid, rmax, t0, nT, acc);
   }
   __syncthreads();
-  const int nb = gridDim.x * gridDim.y;
   const int bid = blockIdx.y * gridDim.x + blockIdx.x;
   const int per = rmax * TC;
-  for (int i = threadIdx.x; i < per; i += kThreads) partials[(size_t)bid * per + i] = acc[i];
-  __threadfence();
+  for (int i = threadIdx.x; i < per; i += blockDim.x) partials[(size_t)bid * per + i] = acc[i];
+}
+
+// ---------------------------------------------------------------------------
+// Wilson loops from shared memory.  Every loop of spatial direction MU lies
+// in the (MU, time) plane through its site, so the lattice splits into
+// independent planes (one per MU and transverse spatial position).  A block
+// stages one plane's MU links and time links in shared memory (coalesced
+// loads), then each thread takes sites of the plane and runs the same line
+// products as wilson_site, reading links from shared memory.  Blocks are
+// persistent: block b takes planes b, b + gridDim.x, ..., so each block's
+// per-(R, T) sums are a fixed function of the grid and the result is
+// reproducible.  blockIdx.y = T chunk.
+// ---------------------------------------------------------------------------
+template <int P, int TC, int NTH>
+__global__ void __launch_bounds__(NTH) k_wilson_plane(Links<P> Ls, Links<P> Lt, Geom g, int rmax, int tmax,
+                                                      double* partials) {
+  using R = typename Real<P>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double acc[kWilsonMaxR * TC];
+  const int lane = threadIdx.x & 31;
+  const int chunk = blockIdx.y;
+  const int t0 = chunk * TC;
+  const int nT = min(TC, tmax - t0);
+  const int nt = g.n[3];
+  for (int i = threadIdx.x; i < kWilsonMaxR * TC; i += NTH) acc[i] = 0.0;
+  // planes: mu in 0..2; transverse positions of the two other spatial axes
+  const int ntr0 = g.n[1] * g.n[2], ntr1 = g.n[0] * g.n[2], ntr2 = g.n[0] * g.n[1];
+  const int nplanes = ntr0 + ntr1 + ntr2;
+  for (int pl = blockIdx.x; pl < nplanes; pl += gridDim.x) {
+    const int mu = pl < ntr0 ? 0 : (pl < ntr0 + ntr1 ? 1 : 2);
+    const int tr = pl - (mu == 0 ? 0 : (mu == 1 ? ntr0 : ntr0 + ntr1));
+    const int nm = mu == 0 ? g.n[0] : (mu == 1 ? g.n[1] : g.n[2]);
+    const int np = nm * nt;
+    Quat<R>* us = reinterpret_cast<Quat<R>*>(smem_raw);   // us[a + nm t]: U_mu(a, t)
+    Quat<R>* ut = us + np;                                // ut[a + nm t]: U_t(a, t)
+    // transverse coordinates (the two spatial axes other than mu, lower first)
+    const int n1st = mu == 0 ? g.n[1] : g.n[0];  // extent of the lower transverse axis
+    const int c1 = tr % n1st, c2 = tr / n1st;
+    __syncthreads();  // the previous plane's readers are done
+    for (int i = threadIdx.x; i < np; i += NTH) {
+      const int a = i % nm, t = i / nm;
+      Site y;
+      y.x0 = mu == 0 ? a : c1;
+      y.x1 = mu == 0 ? c1 : (mu == 1 ? a : c2);
+      y.x2 = mu == 2 ? a : c2;
+      y.x3 = t;
+      y.row = y.x1 + g.n[1] * (y.x2 + g.n[2] * y.x3);
+      const int h = hidx(g, y), par = parity(y);
+      us[i] = Ls.ld(2 * mu + par, h);
+      ut[i] = Lt.ld(6 + par, h);
+    }
+    __syncthreads();
+    for (int base = 0; base < np; base += NTH) {
+      const int i = base + threadIdx.x;
+      const bool valid = i < np;
+      const int a0 = valid ? i % nm : 0, tx = valid ? i / nm : 0;
+      Quat<R> D[TC], C[TC];
+      {
+        Quat<R> pr = qone<R>();
+        int t = tx;
+        for (int k = 0; k < t0; ++k) { pr = qmul(pr, ut[a0 + nm * t]); t = t + 1 == nt ? 0 : t + 1; }
+#pragma unroll
+        for (int j = 0; j < TC; ++j) {
+          if (j < nT) { pr = qmul(pr, ut[a0 + nm * t]); t = t + 1 == nt ? 0 : t + 1; }
+          D[j] = pr;
+          C[j] = qone<R>();
+        }
+      }
+      Quat<R> A = qone<R>();
+      int ar = a0;                                  // a + r - 1
+      int tz = tx + t0 + 1; if (tz >= nt) tz -= nt;   // t + t0 + 1
+      for (int r = 1; r <= rmax; ++r) {
+        A = qmul(A, us[ar + nm * tx]);
+        {
+          int t = tz;
+#pragma unroll
+          for (int j = 0; j < TC; ++j) {
+            if (j < nT) { C[j] = qmul(C[j], us[ar + nm * t]); t = t + 1 == nt ? 0 : t + 1; }
+          }
+        }
+        ar = ar + 1 == nm ? 0 : ar + 1;
+        Quat<R> b = qone<R>();
+        int t = tx;
+        for (int k = 0; k < t0; ++k) { b = qmul(b, ut[ar + nm * t]); t = t + 1 == nt ? 0 : t + 1; }
+        R val[TC];
+#pragma unroll
+        for (int j = 0; j < TC; ++j) {
+          val[j] = R(0);
+          if (j < nT) {
+            b = qmul(b, ut[ar + nm * t]);
+            t = t + 1 == nt ? 0 : t + 1;
+            if (valid) val[j] = qdot(qmul(A, b), qmul(D[j], C[j]));
+          }
+        }
+        int nv = TC;
+        int lo = 0;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          if (nv > 1) {
+            const bool upper = (lane & off) != 0;
+            const int half = nv / 2;
+#pragma unroll
+            for (int k = 0; k < TC / 2; ++k) {
+              if (k < half) {
+                const R send = upper ? val[k] : val[k + half];
+                const R keep = upper ? val[k + half] : val[k];
+                val[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+              }
+            }
+            if (upper) lo += half;
+            nv = half;
+          } else {
+            val[0] += __shfl_xor_sync(0xffffffffu, val[0], off);
+          }
+        }
+        if ((lane & (32 / TC - 1)) == 0 && lo < nT) atomicAdd(&acc[(r - 1) * TC + lo], (double)val[0]);
+      }
+    }
+  }
+  __syncthreads();
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const int per = rmax * TC;
+  for (int i = threadIdx.x; i < per; i += NTH) partials[(size_t)bid * per + i] = acc[i];
+}
+
+// out[(R-1) tmax + (T-1)] from the plane kernel's per-block sums: one block per
+// output adds the gx blocks of T's chunk in a fixed order.
+template <int TC>
+__global__ void __launch_bounds__(kThreads) k_wilson_plane_final(const double* partials, int gx, int rmax, int tmax,
+                                                                 double inv, double* out) {
+  __shared__ double ss[kThreads / 32], sc[kThreads / 32];
+  const int o = blockIdx.x;
+  const int r = o / tmax, t = o % tmax;
+  const int c = t / TC, j = t % TC;
+  const int per = rmax * TC;
+  KSum a;
+  for (int bx = threadIdx.x; bx < gx; bx += blockDim.x)
+    a.add(__ldcg(partials + (size_t)(c * gx + bx) * per + r * TC + j));
+  a = warp_ksum(a);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { ss[warp] = a.s; sc[warp] = a.c; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(counter, 1u) == (unsigned)(nb - 1);
+    KSum tot;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      KSum q;
+      q.s = ss[w];
+      q.c = sc[w];
+      tot = ksum_combine(tot, q);
+    }
+    out[o] = tot.value() * inv;
   }
+}
+
+// out[(R-1) tmax + (T-1)]: one block per output adds the per-block sums of the
+// three directions and all x-blocks of T's chunk, in a fixed order.
+template <int TC>
+__global__ void __launch_bounds__(kThreads) k_wilson_final(const double* partials, int gx, int rmax, int tmax,
+                                                           double inv, double* out) {
+  __shared__ double ss[kThreads / 32], sc[kThreads / 32];
+  const int o = blockIdx.x;
+  const int r = o / tmax, t = o % tmax;
+  const int c = t / TC, j = t % TC;
+  const int per = rmax * TC;
+  const int n = 3 * gx;
+  KSum a;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int m = i / gx, bx = i % gx;
+    a.add(__ldcg(partials + (size_t)((3 * c + m) * gx + bx) * per + r * TC + j));
+  }
+  a = warp_ksum(a);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { ss[warp] = a.s; sc[warp] = a.c; }
   __syncthreads();
-  if (!last) return;
-  const double inv = 1.0 / (3.0 * (double)V);
-  for (int o = threadIdx.x; o < rmax * tmax; o += kThreads) {
-    const int r = o / tmax, t = o % tmax;
-    const int c = t / TC, j = t % TC;
-    KSum a;
-    for (int m = 0; m < 3; ++m)
-      for (int bx = 0; bx < (int)gridDim.x; ++bx)
-        a.add(__ldcg(partials + (size_t)((3 * c + m) * gridDim.x + bx) * per + r * TC + j));
-    out[o] = a.value() * inv;
+  if (threadIdx.x == 0) {
+    KSum tot;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      KSum q;
+      q.s = ss[w];
+      q.c = sc[w];
+      tot = ksum_combine(tot, q);
+    }
+    out[o] = tot.value() * inv;
   }
-  if (threadIdx.x == 0) *counter = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -484,12 +760,10 @@ __global__ void __launch_bounds__(kThreads) k_to_canonical(Links<P> L, Geom g, d
                                                            int64_t s0, int64_t ns) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < 4 * ns; w += stride) {
-    const int64_t s = s0 + (w >> 2);
+    const uint32_t s = (uint32_t)(s0 + (w >> 2));
     const int mu = (int)(w & 3);
-    int x[4];
-    decode_site(g, (uint32_t)s, x);
-    const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
-    const auto q = L.ld(2 * mu + p, s >> 1);
+    const Site x = site_from_index(g, s);
+    const auto q = L.ld(2 * mu + parity(x), hidx(g, x));
     double* o = c + 4 * w;
     o[0] = q.w; o[1] = q.x; o[2] = q.y; o[3] = q.z;
   }
@@ -501,13 +775,11 @@ __global__ void __launch_bounds__(kThreads) k_from_canonical(Links<P> L, Geom g,
   using R = typename Real<P>::T;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < 4 * ns; w += stride) {
-    const int64_t s = s0 + (w >> 2);
+    const uint32_t s = (uint32_t)(s0 + (w >> 2));
     const int mu = (int)(w & 3);
-    int x[4];
-    decode_site(g, (uint32_t)s, x);
-    const int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const Site x = site_from_index(g, s);
     const double* i = c + 4 * w;
-    L.st(2 * mu + p, s >> 1, qmake<R>((R)i[0], (R)i[1], (R)i[2], (R)i[3]));
+    L.st(2 * mu + parity(x), hidx(g, x), qmake<R>((R)i[0], (R)i[1], (R)i[2], (R)i[3]));
   }
 }
 
@@ -531,33 +803,46 @@ template <int P> static Links<P> links_of(void* base, int64_t vh) {
     default: return cudaErrorInvalidValue;                       \
   }
 
+#define SU2_DISPATCH_MU(mu, ...)                          \
+  switch (mu) {                                           \
+    case 0: { constexpr int MU = 0; __VA_ARGS__; break; } \
+    case 1: { constexpr int MU = 1; __VA_ARGS__; break; } \
+    case 2: { constexpr int MU = 2; __VA_ARGS__; break; } \
+    case 3: { constexpr int MU = 3; __VA_ARGS__; break; } \
+    default: return cudaErrorInvalidValue;                \
+  }
+
 cudaError_t launch_init(const LatticeView& v, int start, PhiloxKey key, uint32_t lattice_tag,
                         cudaStream_t st) {
+  const RoundKeys rk = round_keys(key);
   SU2_DISPATCH(v.prec, {
     auto L = links_of<P>(v.links, v.g.vh);
     const int gr = grid_for(k_init<P>, 8 * v.g.vh);
-    k_init<P><<<gr, kThreads, 0, st>>>(L, v.g, start, key, lattice_tag);
+    k_init<P><<<gr, kThreads, 0, st>>>(L, v.g, start, rk, lattice_tag);
   });
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint32_t* sweep_base,
                             uint32_t sweep_off, const HBParams& hp, unsigned long long* stats,
                             cudaStream_t st) {
-  SU2_DISPATCH(v.prec, {
+  SU2_DISPATCH(v.prec, SU2_DISPATCH_MU(mu, {
     auto L = links_of<P>(v.links, v.g.vh);
-    const int gr = grid_for(k_heatbath<P>, v.g.vh);
-    k_heatbath<P><<<gr, kThreads, 0, st>>>(L, v.g, mu, parity, sweep_base, sweep_off, hp, stats);
-  });
+    const int gr = grid_for(k_heatbath<P, MU>, v.g.vh);
+    k_heatbath<P, MU><<<gr, kThreads, 0, st>>>(L, v.g, parity, sweep_base, sweep_off, hp, stats);
+  }));
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_overrelax(const LatticeView& v, int mu, int parity, cudaStream_t st) {
-  SU2_DISPATCH(v.prec, {
+  SU2_DISPATCH(v.prec, SU2_DISPATCH_MU(mu, {
     auto L = links_of<P>(v.links, v.g.vh);
-    const int gr = grid_for(k_overrelax<P>, v.g.vh);
-    k_overrelax<P><<<gr, kThreads, 0, st>>>(L, v.g, mu, parity);
-  });
+    const int gr = grid_for(k_overrelax<P, MU>, v.g.vh);
+    k_overrelax<P, MU><<<gr, kThreads, 0, st>>>(L, v.g, parity);
+  }));
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -567,6 +852,7 @@ cudaError_t launch_plaquette(const LatticeView& v, const Scratch& s, cudaStream_
     const int gr = grid_for(k_plaquette<P>, 2 * v.g.vh);
     k_plaquette<P><<<gr, kThreads, 0, st>>>(L, v.g, s.partials, s.counter, s.out);
   });
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -577,6 +863,7 @@ cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t
     const int gr = grid_for(k_polyakov<P>, nsig);
     k_polyakov<P><<<gr, kThreads, 0, st>>>(L, v.g, s.partials, s.counter, s.out);
   });
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -589,6 +876,7 @@ cudaError_t launch_ape(const LatticeView& src, void* dst, double alpha, cudaStre
     if (gx < 1) gx = 1;
     k_ape<P><<<dim3(gx, 3), kThreads, 0, st>>>(S, D, src.g, alpha);
   });
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -599,28 +887,94 @@ cudaError_t launch_copy_spatial(const LatticeView& src, void* dst, cudaStream_t 
     const int gr = grid_for(k_copy_spatial<P>, 6 * src.g.vh);
     k_copy_spatial<P><<<gr, kThreads, 0, st>>>(S, D);
   });
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int P> struct WilsonChunk { static constexpr int tc = 16; };
+template <> struct WilsonChunk<kF64> { static constexpr int tc = 8; };
+
+// Plane kernel shape per arithmetic precision: T chunk and block size.
+template <int P> struct WPlane { static constexpr int tc = 8, nth = 512; };
+template <> struct WPlane<kF64> { static constexpr int tc = 4, nth = 256; };
+constexpr int kWilsonPlaneSmemMax = 200 * 1024;
+
+template <int P>
+static cudaError_t launch_wilson_plane(const LatticeView& v, const void* spatial, int rmax, int tmax,
+                                       const Scratch& s, cudaStream_t st, bool* used) {
+  using R = typename Real<P>::T;
+  constexpr int TC = WPlane<P>::tc, NTH = WPlane<P>::nth;
+  *used = false;
+  const int nmax = v.g.n[0] > v.g.n[1] ? (v.g.n[0] > v.g.n[2] ? v.g.n[0] : v.g.n[2])
+                                       : (v.g.n[1] > v.g.n[2] ? v.g.n[1] : v.g.n[2]);
+  const int smem = 2 * nmax * v.g.n[3] * (int)sizeof(Quat<R>);
+  if (smem > kWilsonPlaneSmemMax) return cudaSuccess;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_wilson_plane<P, TC, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kWilsonPlaneSmemMax);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson_plane<P, TC, NTH>, NTH, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int nchunks = (tmax + TC - 1) / TC;
+  const int nplanes = v.g.n[1] * v.g.n[2] + v.g.n[0] * v.g.n[2] + v.g.n[0] * v.g.n[1];
+  int64_t gx = (int64_t)device_info().sms * per_sm / nchunks;
+  if (gx > nplanes) gx = nplanes;
+  const int64_t per = (int64_t)rmax * TC;
+  const int64_t cap = (int64_t)kScratchPartials / per / nchunks;
+  if (gx > cap) gx = cap;
+  if (gx < 1) gx = 1;
+  auto Lt = links_of<P>(v.links, v.g.vh);
+  auto Ls = links_of<P>(const_cast<void*>(spatial), v.g.vh);
+  k_wilson_plane<P, TC, NTH><<<dim3((unsigned)gx, nchunks), NTH, smem, st>>>(Ls, Lt, v.g, rmax, tmax, s.partials);
+  count_launches(1);
+  const int64_t V = 2 * v.g.vh;
+  k_wilson_plane_final<TC><<<rmax * tmax, kThreads, 0, st>>>(s.partials, (int)gx, rmax, tmax,
+                                                              1.0 / (3.0 * (double)V), s.out);
+  count_launches(1);
+  *used = true;
   return cudaGetLastError();
 }
 
 cudaError_t launch_wilson(const LatticeView& v, const void* spatial, int rmax, int tmax,
                           const Scratch& s, cudaStream_t st) {
   if (rmax < 1 || rmax > kWilsonMaxR || tmax < 1) return cudaErrorInvalidValue;
+  {
+    bool used = false;
+    cudaError_t e = cudaSuccess;
+    SU2_DISPATCH(v.prec, { e = launch_wilson_plane<P>(v, spatial, rmax, tmax, s, st, &used); });
+    if (e != cudaSuccess || used) return e;
+  }
+  // planes too large for shared memory: global-memory kernel
   SU2_DISPATCH(v.prec, {
-    constexpr int TC = P == kF64 ? 4 : 8;
+    constexpr int TC = WilsonChunk<P>::tc;
     auto Lt = links_of<P>(v.links, v.g.vh);
     auto Ls = links_of<P>(const_cast<void*>(spatial), v.g.vh);
     const int nchunks = (tmax + TC - 1) / TC;
     const int64_t V = 2 * v.g.vh;
-    int gx = grid_for(k_wilson<P, TC>, V);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson<P, TC>, kWilsonThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    // all (chunk, direction) slices together fill the machine once
+    int64_t gx = (int64_t)device_info().sms * per_sm / (3 * nchunks);
+    const int64_t need = (V + kWilsonThreads - 1) / kWilsonThreads;
+    if (gx > need) gx = need;
     // keep one partial set per block within the scratch buffer
     const int64_t per = (int64_t)rmax * TC;
-    const int64_t max_blocks = (int64_t)kScratchPartials / per;
-    const int64_t cap = max_blocks / (3 * nchunks);
-    if (gx > cap) gx = (int)cap;
-    if (gx < 1) return cudaErrorInvalidValue;
-    k_wilson<P, TC><<<dim3(gx, 3 * nchunks), kThreads, 0, st>>>(Ls, Lt, v.g, rmax, tmax,
-                                                                s.partials, s.counter, s.out);
+    const int64_t cap = (int64_t)kScratchPartials / per / (3 * nchunks);
+    if (gx > cap) gx = cap;
+    if (gx < 1) gx = 1;
+    k_wilson<P, TC><<<dim3((unsigned)gx, 3 * nchunks), kWilsonThreads, 0, st>>>(Ls, Lt, v.g, rmax, tmax, s.partials);
+    count_launches(1);
+    k_wilson_final<TC><<<rmax * tmax, kThreads, 0, st>>>(s.partials, (int)gx, rmax, tmax, 1.0 / (3.0 * (double)V),
+                                                         s.out);
   });
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -631,6 +985,7 @@ cudaError_t launch_to_canonical(const LatticeView& v, double* canon, int64_t s0,
     const int gr = grid_for(k_to_canonical<P>, 4 * ns);
     k_to_canonical<P><<<gr, kThreads, 0, st>>>(L, v.g, canon, s0, ns);
   });
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -641,11 +996,13 @@ cudaError_t launch_from_canonical(const LatticeView& v, const double* canon, int
     const int gr = grid_for(k_from_canonical<P>, 4 * ns);
     k_from_canonical<P><<<gr, kThreads, 0, st>>>(L, v.g, canon, s0, ns);
   });
+  count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_add_u32(uint32_t* p, uint32_t v, cudaStream_t st) {
   k_add_u32<<<1, 1, 0, st>>>(p, v);
+  count_launches(1);
   return cudaGetLastError();
 }
 

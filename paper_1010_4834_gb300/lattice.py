@@ -13,14 +13,28 @@ from . import _lib
 from ._lib import check, dims_arg
 
 
+_CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy: the implicit default stream
+
+
 def _stream_ptr(stream):
+    """torch's stream as a cudaStream_t.  torch's default stream has handle 0,
+    which the C ABI reads as "create a private stream"; pass the legacy
+    default stream's handle instead so the work stays ordered with torch."""
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
-    return C.c_void_p(int(s.cuda_stream))
+    h = int(s.cuda_stream)
+    return C.c_void_p(h if h != 0 else _CUDA_STREAM_LEGACY)
 
 
 def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def kernel_launches():
+    """Kernels libsu2 has launched in this process."""
+    n = C.c_uint64()
+    check(_lib.load().su2_kernel_launches(C.byref(n)))
+    return n.value
 
 
 class Lattice:
@@ -86,6 +100,18 @@ class Lattice:
 
     def sweep(self, n=1):
         check(_lib.load().su2_heatbath_sweep(self._h, int(n)))
+
+    def restart(self, start="hot"):
+        check(_lib.load().su2_restart(self._h, _lib.START[start]))
+
+    def sweep_measure(self, n, out=None):
+        """n x (sweep, plaquette, Polyakov); returns an (n, 4) array:
+        plaquette all / spatial / space-time, Polyakov loop."""
+        if out is None:
+            out = np.empty((n, 4))
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size >= 4 * n
+        check(_lib.load().su2_sweep_measure(self._h, int(n), _dptr(out)))
+        return out
 
     def substep(self, mu, parity, sweep_index):
         check(_lib.load().su2_heatbath_substep(self._h, int(mu), int(parity), int(sweep_index)))

@@ -362,3 +362,42 @@ def test_full_size_64_sampled():
     p = lat.plaquette()
     assert abs(p[0] - oracle.plaquette(list(dims), U1)[0]) < 2e-7
     lat.close()
+
+
+# ---------------------------------------------------------------------------
+def test_sweep_measure_restart_and_launch_count():
+    from paper_1010_4834_gb300 import kernel_launches
+    dims = (4, 4, 6, 4)
+    a = Lattice(dims, 2.3, seed=5, start="hot", prec="f64")
+    b = Lattice(dims, 2.3, seed=5, start="hot", prec="f64")
+    n0 = kernel_launches()
+    hist = a.sweep_measure(6)
+    assert kernel_launches() - n0 == 6 * (8 + 1 + 2)      # 8 substeps, counter, plaquette, Polyakov
+    ref = []
+    for _ in range(6):
+        b.sweep(1)
+        ref.append(list(b.plaquette()) + [b.polyakov()])
+    np.testing.assert_array_equal(hist, np.array(ref))
+    assert a.sweep_count == 6
+    a.restart("hot")
+    assert a.sweep_count == 0
+    fresh = Lattice(dims, 2.3, seed=5, start="hot", prec="f64")
+    assert np.array_equal(a.get_links(), fresh.get_links())
+    for lat in (a, b, fresh):
+        lat.close()
+
+
+def test_work_is_ordered_on_the_torch_stream():
+    import torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        lat = Lattice((8, 8, 8, 8), 2.4, seed=3, start="hot", prec="f32")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lat.sweep(16)
+        e1.record()
+        e1.synchronize()
+        # the events bracket the sweeps: a 16-sweep run takes measurable time
+        assert e0.elapsed_time(e1) > 0.005
+        assert lat.sweep_count == 16
+        lat.close()
