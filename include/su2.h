@@ -178,6 +178,25 @@ int su2_overrelax_sweep(su2_lattice* h, int n);
 int su2_plaquette(su2_lattice* h, double out[3]);
 
 /*
+ * The paper has no counterpart to this entry point: it is su2_plaquette for
+ * callers that cannot allocate device memory -- a framework whose caching
+ * allocator must own every device byte, a service with a fixed memory
+ * budget, or a loop that cannot accept cudaMalloc's implicit device
+ * synchronisation.  It needs no handle: `links` is a device pointer to a link
+ * store in the layout described above (for a handle made with
+ * su2_init_external it is the start of the caller's buffer), `dims` and
+ * `prec` describe it, out[3] (host) receives what su2_plaquette returns.  The
+ * reduction scratch is a fixed 64 KiB array in the library's device memory
+ * (one partial per block, at most 4096 blocks; SU2_EINVAL if a device would
+ * need more).  The call allocates nothing.  The first call on each device
+ * looks the array's address up with that device current; make it before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race, so serialise them.  `cuda_stream` NULL is the legacy default stream.
+ * Synchronises the stream.
+ */
+int su2_plaquette_static(const void* links, const int dims[4], int prec, double out[3], void* cuda_stream);
+
+/*
  * Signed Polyakov loop (Section 2, Eqs. 14-15): mean over the N0 N1 N2
  * spatial sites of (1/2) Tr of the product of time links in increasing t.
  * Synchronises.

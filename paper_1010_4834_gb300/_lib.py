@@ -52,6 +52,7 @@ SIGNATURES = {
     "su2_kernel_launches": (_i, [C.POINTER(_u64)]),
     "su2_overrelax_sweep": (_i, [_vp, _i]),
     "su2_plaquette": (_i, [_vp, _dp]),
+    "su2_plaquette_static": (_i, [_vp, _ip, _i, _dp, _vp]),
     "su2_polyakov": (_i, [_vp, _dp]),
     "su2_ape_smear": (_i, [_vp, _d, _i]),
     "su2_wilson_loops": (_i, [_vp, _i, _i, _i, _dp]),
