@@ -168,9 +168,12 @@ def substep_launch_seconds(torch, lat, sweeps=4):
 
 
 def source_sha():
+    """Hash of the heat-bath kernel's sources and build flags."""
     h = hashlib.sha256()
-    for f in ("su2_device.cuh", "su2_kernels.cu"):
-        with open(os.path.join(ROOT, "paper_1010_4834_gb300", "csrc", f), "rb") as fh:
+    pkg = os.path.join(ROOT, "paper_1010_4834_gb300")
+    for f in (os.path.join(pkg, "csrc", "su2_device.cuh"), os.path.join(pkg, "csrc", "su2_kernels.cu"),
+              os.path.join(pkg, "build.py")):
+        with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

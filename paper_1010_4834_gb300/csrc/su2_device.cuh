@@ -221,37 +221,62 @@ struct HBParams {
   int sampler;           // 0 Kennedy-Pendleton, 1 Creutz
 };
 
-// Sampled a0 (Section 2, Eq. 8) for alpha = beta k.  Trial n = 1..max_tries
-// uses Philox draw n of this link.  Returns the trial that accepted, 0 if none.
+// One trial n of the a0 draw (Section 2, Eq. 8) for alpha = beta k, using
+// Philox draw n of this link; inv2a = 1/(2 alpha), e = exp(-2 alpha) (Creutz).
 //   Kennedy-Pendleton: delta = -(ln u0 + cos^2(2 pi u1) ln u2) / (2 alpha),
 //                      accept if u3^2 <= 1 - delta, a0 = 1 - 2 delta.
 //   Creutz:            a0 = 1 + ln(e^{-2 alpha} + (1 - e^{-2 alpha}) u0)/alpha,
 //                      accept if u1^2 <= 1 - a0^2.
 template <class R>
-__device__ __forceinline__ int sample_a0(R alpha, uint4 ctr, const HBParams& hp, R* a0) {
+__device__ __forceinline__ bool trial_a0(R alpha, R inv2a, R e, uint4 ctr, int n, const HBParams& hp, R* a0) {
   using M = Math<R>;
-  const R inv2a = M::div(R(0.5), alpha);
-  const int sampler = hp.sampler;
-  const R e = sampler ? M::exp(R(-2) * alpha) : R(0);
-  for (int n = 1; n <= hp.max_tries; ++n) {
-    ctr.w = (uint32_t)n;
-    const uint4 r = philox(ctr, hp.rk);
-    if (sampler == 0) {
-      const R u0 = u01<R>(r.x), u1 = u01<R>(r.y), u2 = u01<R>(r.z), u3 = u01<R>(r.w);
-      const R c = M::cos2pi(u1);
-      const R delta = -(M::log_fast(u0) + c * c * M::log_fast(u2)) * inv2a;
-      if (u3 * u3 <= R(1) - delta) { *a0 = R(1) - R(2) * delta; return n; }
-    } else {
-      const R u0 = u01<R>(r.x), u1 = u01<R>(r.y);
-      const R cand = R(1) + M::div(M::log_fast(e + (R(1) - e) * u0), alpha);
-      if (u1 * u1 <= R(1) - cand * cand) { *a0 = cand; return n; }
-    }
+  ctr.w = (uint32_t)n;
+  const uint4 r = philox(ctr, hp.rk);
+  if (hp.sampler == 0) {
+    const R u0 = u01<R>(r.x), u1 = u01<R>(r.y), u2 = u01<R>(r.z), u3 = u01<R>(r.w);
+    const R c = M::cos2pi(u1);
+    const R delta = -(M::log_fast(u0) + c * c * M::log_fast(u2)) * inv2a;
+    if (u3 * u3 <= R(1) - delta) { *a0 = R(1) - R(2) * delta; return true; }
+  } else {
+    const R u0 = u01<R>(r.x), u1 = u01<R>(r.y);
+    const R cand = R(1) + M::div(M::log_fast(e + (R(1) - e) * u0), alpha);
+    if (u1 * u1 <= R(1) - cand * cand) { *a0 = cand; return true; }
   }
+  return false;
+}
+
+// The per-link constants of the trials.
+template <class R> __device__ __forceinline__ R trial_inv2a(R alpha) { return Math<R>::div(R(0.5), alpha); }
+template <class R> __device__ __forceinline__ R trial_e(R alpha, int sampler) {
+  return sampler ? Math<R>::exp(R(-2) * alpha) : R(0);
+}
+
+// Trials first..max_tries; returns the trial that accepted, 0 if none.
+template <class R>
+__device__ __forceinline__ int sample_a0_from(int first, R alpha, R inv2a, R e, uint4 ctr, const HBParams& hp, R* a0) {
+  for (int n = first; n <= hp.max_tries; ++n)
+    if (trial_a0<R>(alpha, inv2a, e, ctr, n, hp, a0)) return n;
   return 0;
 }
 
-// Full heat-bath draw for one link given its staple sum (Section 2, Eqs. 5-9):
-// X with x0 = a0 and uniform direction (Philox draw 0), new link X * Sigma / k.
+// The accepted link (Section 2, Eqs. 7, 9): X with x0 = a0 and a uniform
+// direction from Philox draw 0 (cos theta = 2 u0 - 1, phi = 2 pi u1), times
+// W = Sigma / k.
+template <class R>
+__device__ __forceinline__ Quat<R> compose_link(R a0, const Quat<R>& w, uint4 ctr, const HBParams& hp) {
+  using M = Math<R>;
+  ctr.w = 0u;
+  const uint4 r = philox(ctr, hp.rk);
+  const R cos_t = R(2) * u01<R>(r.x) - R(1);
+  const R sin_t = M::sqrt0(R(1) - cos_t * cos_t);
+  R sp, cp;
+  M::sincos2pi(u01<R>(r.y), &sp, &cp);
+  const R rad = M::sqrt0(R(1) - a0 * a0);
+  const Quat<R> x = qmake<R>(a0, rad * sin_t * cp, rad * sin_t * sp, rad * cos_t);
+  return qmul(x, w);
+}
+
+// Full heat-bath draw for one link given its staple sum (Section 2, Eqs. 5-9).
 // alpha < 1e-12: Haar link from draw 1.  `ctr` holds (site, mu | lattice_tag,
 // sweep, -).  Returns trials used; 0 means every trial failed, `out` is not
 // written and the caller keeps the old link; -1 marks the Haar branch.
@@ -268,17 +293,9 @@ __device__ __forceinline__ int heatbath_draw(const Quat<R>& sigma, uint4 ctr, co
     return -1;
   }
   R a0;
-  const int n = sample_a0<R>(alpha, ctr, hp, &a0);
+  const int n = sample_a0_from<R>(1, alpha, trial_inv2a(alpha), trial_e(alpha, hp.sampler), ctr, hp, &a0);
   if (n == 0) return 0;
-  ctr.w = 0u;
-  const uint4 r = philox(ctr, hp.rk);
-  const R cos_t = R(2) * u01<R>(r.x) - R(1);
-  const R sin_t = M::sqrt0(R(1) - cos_t * cos_t);
-  R sp, cp;
-  M::sincos2pi(u01<R>(r.y), &sp, &cp);
-  const R rad = M::sqrt0(R(1) - a0 * a0);
-  const Quat<R> x = qmake<R>(a0, rad * sin_t * cp, rad * sin_t * sp, rad * cos_t);
-  *out = qmul(x, qscale(sigma, invk));
+  *out = compose_link<R>(a0, qscale(sigma, invk), ctr, hp);
   return n;
 }
 

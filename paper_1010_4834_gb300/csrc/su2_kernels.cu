@@ -236,23 +236,109 @@ __global__ void __launch_bounds__(kThreads) k_init(Links<P> L, Geom g, int start
 // ---------------------------------------------------------------------------
 // Heat-bath substep (Section 2 Eqs. 5-9, 11; Section 4 checkerboard): one
 // thread per link of direction MU on the parity-p sublattice.
+//
+// Most links accept their first a0 trial, but a warp would repeat the trial
+// loop until its slowest lane accepts.  So every lane makes trial 1 inline;
+// a link that rejects it goes to a block-wide shared-memory queue (its
+// W = Sigma/k, alpha, index and site), which the whole block drains every
+// kDeferEvery iterations with trials 2, 3, ...  The draws and their order are
+// those of the plain loop, so results are identical; only the schedule
+// differs.  A full queue falls back to finishing the link inline.
 // ---------------------------------------------------------------------------
+constexpr int kDeferCap = 512;
+constexpr int kDeferEvery = 8;
+
+template <class R> struct Deferred {
+  Quat<R> w;
+  R alpha;
+  int h;
+  uint32_t site;
+};
+
+template <class R>
+__device__ __forceinline__ int finish_deferred(const Deferred<R>& d, uint4 ctr, const HBParams& hp, Quat<R>* out) {
+  R a0;
+  const int n = sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0);
+  if (n) *out = compose_link<R>(a0, d.w, ctr, hp);
+  return n;
+}
+
 template <int P, int MU>
 __global__ void __launch_bounds__(kThreads, Occ<P>::hb)
     k_heatbath(Links<P> L, Geom g, int p, const uint32_t* sweep_base, uint32_t sweep_off,
                const __grid_constant__ HBParams hp, unsigned long long* stats) {
   using R = typename Real<P>::T;
+  using M = Math<R>;
+  __shared__ Deferred<R> queue[kDeferCap];
+  __shared__ int qn;
   const R beta = (R)hp.beta;
   const uint32_t sweep = (sweep_base ? *sweep_base : 0u) + sweep_off;
+  const uint32_t tag = (uint32_t)MU | hp.lattice_tag;
   unsigned int trials = 0, capped = 0, haar = 0;
+  if (threadIdx.x == 0) qn = 0;
+  __syncthreads();
+  const int vh = (int)g.vh;
   const int stride = gridDim.x * blockDim.x;
-  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.vh; h += stride) {
-    const Site x = site_from_half(g, (uint32_t)h, p);
-    const int n = heatbath_site<P, MU, true>(L, g, x, h, p, sweep, hp, beta);
-    if (stats) {
-      trials += n > 0 ? (unsigned)n : (n == 0 ? (unsigned)hp.max_tries : 0u);
-      capped += n == 0;
-      haar += n < 0;
+  int it = 0;
+  for (int base = blockIdx.x * blockDim.x; base < vh; base += stride, ++it) {
+    const int h = base + threadIdx.x;
+    if (h < vh) {
+      const Site x = site_from_half(g, (uint32_t)h, p);
+      const Quat<R> sig = staple<P, MU, 0xF, true>(L, g, x, h, p);
+      const uint32_t site = site_index(g, x);
+      const uint4 ctr = make_uint4(site, tag, sweep, 0u);
+      const R k2 = qdot(sig, sig);
+      const R invk = M::rsqrt(k2);
+      const R alpha = beta * k2 * invk;
+      if (!(alpha >= R(1e-12))) {
+        uint4 c = ctr;
+        c.w = 1u;
+        L.st(2 * MU + p, h, haar_from<R>(philox(c, hp.rk)));
+        haar += 1;
+      } else {
+        const R inv2a = trial_inv2a(alpha);
+        const R e = trial_e(alpha, hp.sampler);
+        const Quat<R> w = qscale(sig, invk);
+        R a0;
+        if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0)) {
+          L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, hp));
+          trials += 1;
+        } else if (hp.max_tries > 1) {
+          const int slot = atomicAdd(&qn, 1);
+          Deferred<R> d;
+          d.w = w;
+          d.alpha = alpha;
+          d.h = h;
+          d.site = site;
+          if (slot < kDeferCap) {
+            queue[slot] = d;
+          } else {
+            Quat<R> nl;
+            const int n = finish_deferred<R>(d, ctr, hp, &nl);
+            if (n) L.st(2 * MU + p, h, nl);
+            trials += n ? (unsigned)n : (unsigned)hp.max_tries;
+            capped += n == 0;
+          }
+        } else {
+          trials += 1;
+          capped += 1;
+        }
+      }
+    }
+    if ((it % kDeferEvery) == kDeferEvery - 1 || base + stride >= vh) {
+      __syncthreads();
+      const int n = min(qn, kDeferCap);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Deferred<R> d = queue[i];
+        Quat<R> nl;
+        const int t = finish_deferred<R>(d, make_uint4(d.site, tag, sweep, 0u), hp, &nl);
+        if (t) L.st(2 * MU + p, d.h, nl);
+        trials += t ? (unsigned)t : (unsigned)hp.max_tries;
+        capped += t == 0;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) qn = 0;
+      __syncthreads();
     }
   }
   if (stats) {
