@@ -266,12 +266,26 @@ int su2_batch_destroy(su2_batch* b);
 int su2_batch_set_options(su2_batch* b, int max_tries, int sampler);
 
 /*
- * n heat-bath sweeps of every lattice, in one persistent kernel launch per
- * call (replayed from a CUDA graph).  Lattices advance independently; within
- * a lattice the eight substeps are ordered by bounded device-side barriers.
- * SU2_ETIMEOUT if a barrier gave up (the sweep results are then invalid).
+ * n heat-bath sweeps of every lattice, in one persistent cooperative kernel
+ * launch per call (replayed from a CUDA graph).  The grid is split into G
+ * groups of CTAs; each group sweeps its share of the lattices one lattice at
+ * a time, the eight substeps of a lattice ordered by bounded barriers among
+ * the group's CTAs.  Results do not depend on G (every draw is keyed by
+ * lattice, sweep, site and direction).  SU2_ETIMEOUT if a barrier wait gave
+ * up; the lattices are then invalid and the handle should be destroyed.
  */
 int su2_batch_sweep(su2_batch* b, int n);
+
+/*
+ * The schedule's group count G (1 <= G <= min(lattices, co-resident CTAs)).
+ * The default gives each group about 16 CTAs.
+ * su2_batch_tune times `sweeps` sweeps for a set of candidate G on a scratch
+ * copy of the links (the chain is not advanced; it allocates and frees that
+ * copy), keeps the fastest and returns it in *groups (may be NULL).
+ */
+int su2_batch_set_groups(su2_batch* b, int groups);
+int su2_batch_groups(su2_batch* b, int* groups);
+int su2_batch_tune(su2_batch* b, int sweeps, int* groups);
 
 /* out[3*i + k]: su2_plaquette of lattice i.  Synchronises. */
 int su2_batch_plaquette(su2_batch* b, double* out);

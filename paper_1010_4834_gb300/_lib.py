@@ -66,6 +66,9 @@ SIGNATURES = {
     "su2_batch_destroy": (_i, [_vp]),
     "su2_batch_set_options": (_i, [_vp, _i, _i]),
     "su2_batch_sweep": (_i, [_vp, _i]),
+    "su2_batch_set_groups": (_i, [_vp, _i]),
+    "su2_batch_groups": (_i, [_vp, _ip]),
+    "su2_batch_tune": (_i, [_vp, _i, _ip]),
     "su2_batch_plaquette": (_i, [_vp, _dp]),
     "su2_batch_polyakov": (_i, [_vp, _dp]),
     "su2_batch_get_links": (_i, [_vp, _i, _dp]),

@@ -3,13 +3,23 @@
 //
 // The heat bath of each lattice follows Section 2 (Eqs. 5-9, 11) and the
 // checkerboard of Section 4 exactly as for a single lattice; lattice i uses
-// Philox lattice_id = i.  All lattices advance through the same substep
-// sequence: every thread of the grid takes items (one link each) from the
-// concatenation of all lattices' (direction, parity) class, and a grid-wide
-// barrier separates the substeps.  The barrier waits are bounded in time:
-// a block that gives up raises a device error flag, every block then leaves,
-// and the host reports SU2_ETIMEOUT.  The grid is launched cooperatively so
-// that all blocks are co-resident.
+// Philox lattice_id = i, so every link's draws are fixed by (lattice, sweep,
+// site, direction) and the result does not depend on the schedule below.
+//
+// Schedule.  The cooperative grid is split into G groups of CTAs.  The
+// lattices are dealt to the groups largest first, each to the group with the
+// least work so far; a group sweeps its lattices one after another, all n
+// sweeps of one lattice before the next.  Substeps within a lattice are
+// ordered by a barrier among the group's CTAs only, which is cheaper than a
+// grid-wide barrier, and the G lattices in flight are re-read from L2 rather
+// than HBM between substeps when they fit.  G defaults to about 16 CTAs per
+// group; su2_batch_tune times candidate G on a scratch copy of the links.
+//
+// Every barrier wait is bounded twice (global timer and iteration count); a
+// wait that runs out raises a device error flag, all blocks leave, and the
+// host reports SU2_ETIMEOUT.  Cooperative launch guarantees that all CTAs are
+// co-resident.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -26,14 +36,18 @@ struct BatchLattice {
   Geom g;
   void* links;
   double beta;
-  int64_t item_begin;  // prefix sum of V/2 over the lattices before this one
 };
 
-struct BarrierState {
+// One barrier per group, each on its own 128-byte line.
+struct GroupBarrier {
   unsigned int count;
   unsigned int gen;
-  int err;            // 1: a barrier wait timed out
-  unsigned int extra; // arrivals the barrier waits for beyond gridDim.x (fault injection)
+  unsigned int pad[30];
+};
+
+struct BatchCtl {
+  int err;             // 1: a barrier wait timed out
+  unsigned int extra;  // arrivals a barrier waits for beyond its group (fault injection)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -42,20 +56,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier with a time limit.  Returns false if any block timed out.
-__device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned long long timeout_ns) {
+// Barrier among the `n` CTAs of one group.  Returns false if any wait timed out.
+__device__ __forceinline__ bool group_barrier(GroupBarrier* gb, unsigned int n, BatchCtl* ctl,
+                                              unsigned long long timeout_ns) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &bs->gen;
-    volatile int* verr = &bs->err;
+    volatile unsigned int* vgen = &gb->gen;
+    volatile int* verr = &ctl->err;
     const unsigned int g = *vgen;
     __threadfence();
-    const unsigned int arrived = atomicAdd(&bs->count, 1u) + 1u;
-    if (arrived == gridDim.x + bs->extra) {
-      bs->count = 0;
+    const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
+    if (arrived == n + ctl->extra) {
+      gb->count = 0;
       __threadfence();
-      atomicExch(&bs->gen, g + 1u);
+      atomicExch(&gb->gen, g + 1u);
     } else {
       // bounded twice over: by the global timer and by an iteration count
       const unsigned long long t0 = global_ns();
@@ -63,7 +78,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned long lon
       while (*vgen == g) {
         if (*verr) break;
         if (global_ns() - t0 > timeout_ns || ++spins > (1ull << 24)) {
-          atomicExch(&bs->err, 1);
+          atomicExch(&ctl->err, 1);
           break;
         }
         __nanosleep(100);
@@ -76,45 +91,113 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned long lon
   return ok != 0;
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) k_batch_sweep(const BatchLattice* __restrict__ desc, int nlat,
-                                                     int64_t total, int nsweeps,
-                                                     const uint32_t* sweep_base,
-                                                     const __grid_constant__ HBParams hp,
-                                                     BarrierState* bs,
-                                                     unsigned long long timeout_ns) {
+constexpr int kBatchThreads = 256;
+constexpr int kBatchQueue = 512;
+
+template <class R> struct BDeferred {
+  Quat<R> w;
+  R alpha;
+  int h;
+  uint32_t site;
+};
+
+// One substep (MU, p) of one lattice by the CTAs of a group: trial 1 inline,
+// rejected links queued and finished by the whole block at the end.  Links
+// are read with coherent loads (other CTAs of the group wrote them before the
+// last barrier).
+template <int P, int MU>
+__device__ __forceinline__ void batch_substep(const Links<P>& L, const Geom& g, int p, int rank, int cpg,
+                                              uint32_t sweep, uint32_t tag, typename Real<P>::T beta,
+                                              const HBParams& hp, BDeferred<typename Real<P>::T>* queue, int* qn) {
   using R = typename Real<P>::T;
+  using M = Math<R>;
+  const int vh = (int)g.vh;
+  for (int base = rank * kBatchThreads; base < vh; base += cpg * kBatchThreads) {
+    const int h = base + threadIdx.x;
+    if (h >= vh) continue;
+    const Site x = site_from_half(g, (uint32_t)h, p);
+    const Quat<R> sig = staple<P, MU, 0xF, false>(L, g, x, h, p);
+    const uint32_t site = site_index(g, x);
+    const uint4 ctr = make_uint4(site, tag, sweep, 0u);
+    const R k2 = qdot(sig, sig);
+    const R invk = M::rsqrt(k2);
+    const R alpha = beta * k2 * invk;
+    if (!(alpha >= R(1e-12))) {
+      uint4 c = ctr;
+      c.w = 1u;
+      L.st(2 * MU + p, h, haar_from<R>(philox(c, hp.rk)));
+      continue;
+    }
+    const R inv2a = trial_inv2a(alpha);
+    const R e = trial_e(alpha, hp.sampler);
+    const Quat<R> w = qscale(sig, invk);
+    R a0;
+    if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0)) {
+      L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, hp));
+    } else if (hp.max_tries > 1) {
+      const int slot = atomicAdd(qn, 1);
+      if (slot < kBatchQueue) {
+        BDeferred<R> d;
+        d.w = w;
+        d.alpha = alpha;
+        d.h = h;
+        d.site = site;
+        queue[slot] = d;
+      } else if (sample_a0_from<R>(2, alpha, inv2a, e, ctr, hp, &a0)) {
+        L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, hp));
+      }
+    }
+  }
+  __syncthreads();
+  const int n = min(*qn, kBatchQueue);
+  for (int i = threadIdx.x; i < n; i += kBatchThreads) {
+    const BDeferred<R> d = queue[i];
+    const uint4 ctr = make_uint4(d.site, tag, sweep, 0u);
+    R a0;
+    if (sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0))
+      L.st(2 * MU + p, d.h, compose_link<R>(a0, d.w, ctr, hp));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *qn = 0;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kBatchThreads)
+    k_batch_groups(const BatchLattice* __restrict__ desc, const int* __restrict__ order,
+                   const int2* __restrict__ plan, int groups, int cpg, int nsweeps, const uint32_t* sweep_base,
+                   const __grid_constant__ HBParams hp, GroupBarrier* bars, BatchCtl* ctl,
+                   unsigned long long timeout_ns) {
+  using R = typename Real<P>::T;
+  __shared__ BDeferred<R> queue[kBatchQueue];
+  __shared__ int qn;
+  const int group = blockIdx.x / cpg;
+  if (group >= groups) return;
+  const int rank = blockIdx.x - group * cpg;
+  if (threadIdx.x == 0) qn = 0;
+  __syncthreads();
   const uint32_t sweep0 = *sweep_base;
-  const int64_t T = (int64_t)gridDim.x * blockDim.x;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int sw = 0; sw < nsweeps; ++sw) {
-    for (int mu = 0; mu < 4; ++mu) {
-      for (int p = 0; p < 2; ++p) {
-        int l = 0;
-        int64_t next = nlat > 1 ? desc[1].item_begin : total;
-        for (int64_t it = tid; it < total; it += T) {
-          while (it >= next) {
-            ++l;
-            next = l + 1 < nlat ? desc[l + 1].item_begin : total;
-          }
-          const BatchLattice& d = desc[l];
-          Links<P> L;
-          L.p = reinterpret_cast<decltype(L.p)>(d.links);
-          L.vh = d.g.vh;
-          const int h = (int)(it - d.item_begin);
-          const Site x = site_from_half(d.g, (uint32_t)h, p);
-          HBParams lp = hp;
-          lp.lattice_tag = (uint32_t)l << 2;
-          const uint32_t sweep = sweep0 + (uint32_t)sw;
-          const R beta = (R)d.beta;
+  const int2 pl = plan[group];
+  for (int li = 0; li < pl.y; ++li) {
+    const int l = order[pl.x + li];
+    const Geom g = desc[l].g;
+    Links<P> L;
+    L.p = reinterpret_cast<decltype(L.p)>(desc[l].links);
+    L.vh = g.vh;
+    const R beta = (R)desc[l].beta;
+    const uint32_t ltag = (uint32_t)l << 2;
+    for (int sw = 0; sw < nsweeps; ++sw) {
+      const uint32_t sweep = sweep0 + (uint32_t)sw;
+      for (int mu = 0; mu < 4; ++mu) {
+        for (int p = 0; p < 2; ++p) {
+          const uint32_t tag = (uint32_t)mu | ltag;
           switch (mu) {
-            case 0: heatbath_site<P, 0, false>(L, d.g, x, h, p, sweep, lp, beta); break;
-            case 1: heatbath_site<P, 1, false>(L, d.g, x, h, p, sweep, lp, beta); break;
-            case 2: heatbath_site<P, 2, false>(L, d.g, x, h, p, sweep, lp, beta); break;
-            default: heatbath_site<P, 3, false>(L, d.g, x, h, p, sweep, lp, beta); break;
+            case 0: batch_substep<P, 0>(L, g, p, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            case 1: batch_substep<P, 1>(L, g, p, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            case 2: batch_substep<P, 2>(L, g, p, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            default: batch_substep<P, 3>(L, g, p, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
           }
+          if (!group_barrier(bars + group, (unsigned)cpg, ctl, timeout_ns)) return;
         }
-        if (!grid_barrier(bs, timeout_ns)) return;
       }
     }
   }
@@ -133,10 +216,13 @@ struct su2_batch {
   std::vector<int> dims;
   std::vector<double> betas;
   std::vector<BatchLattice> desc;
-  int64_t total_items;
   void* base;
+  size_t links_bytes;  // the lattices' stores occupy [base, base + links_bytes)
   BatchLattice* d_desc;
-  BarrierState* d_bar;
+  int* d_order;
+  int2* d_plan;
+  GroupBarrier* d_bars;
+  BatchCtl* d_ctl;
   uint32_t* d_sweep;
   Scratch scratch;
   double* d_results;
@@ -146,17 +232,20 @@ struct su2_batch {
   cudaStream_t cap_stream;
   cudaGraphExec_t graph;
   int graph_n;
-  int grid;
+  int grid;    // co-resident CTAs
+  int groups;  // current G
   unsigned long long timeout_ns;
 };
 
 namespace {
 
+constexpr int kMaxGroups = 1024;
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 template <int P> int occupancy_blocks() {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_sweep<P>, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_groups<P>, kBatchThreads, 0);
   return per_sm;
 }
 
@@ -197,30 +286,82 @@ void drop_graph(su2_batch* b) {
   b->graph_n = 0;
 }
 
-cudaError_t enqueue_batch_sweep(su2_batch* b, int n, cudaStream_t st) {
+// Deal the lattices to G groups, largest first, each to the least loaded
+// group; write the per-group (first, count) plan and the lattice order.
+void make_plan(const su2_batch* b, int G, std::vector<int>& order, std::vector<int2>& plan) {
+  std::vector<int> idx(b->n);
+  for (int i = 0; i < b->n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return b->desc[a].g.vh > b->desc[c].g.vh; });
+  std::vector<int64_t> load(G, 0);
+  std::vector<std::vector<int>> members(G);
+  for (int i : idx) {
+    int best = 0;
+    for (int gi = 1; gi < G; ++gi)
+      if (load[gi] < load[best]) best = gi;
+    members[best].push_back(i);
+    load[best] += b->desc[i].g.vh;
+  }
+  order.clear();
+  plan.assign(G, make_int2(0, 0));
+  for (int gi = 0; gi < G; ++gi) {
+    plan[gi].x = (int)order.size();
+    plan[gi].y = (int)members[gi].size();
+    order.insert(order.end(), members[gi].begin(), members[gi].end());
+  }
+}
+
+// Default G: about 16 CTAs per group (a group barrier costs more the more
+// CTAs it joins, and more groups keep more lattices in flight), no more
+// groups than lattices.  su2_batch_tune measures instead of guessing.
+int default_groups(const su2_batch* b) {
+  int64_t G = std::max(1, b->grid / 16);
+  G = std::max<int64_t>(1, std::min<int64_t>(G, b->n));
+  return (int)std::min<int64_t>(G, kMaxGroups);
+}
+
+int set_groups(su2_batch* b, int G) {
+  std::vector<int> order;
+  std::vector<int2> plan;
+  make_plan(b, G, order, plan);
+  SU2_CU(cudaMemcpyAsync(b->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  SU2_CU(cudaMemcpyAsync(b->d_plan, plan.data(), plan.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  SU2_CU(cudaStreamSynchronize(b->stream));
+  b->groups = G;
+  drop_graph(b);
+  return SU2_OK;
+}
+
+cudaError_t launch_groups(const su2_batch* b, const BatchLattice* d_desc, int n, cudaStream_t st) {
   const HBParams hp = batch_hp(b);
+  const int G = b->groups;
+  const int cpg = std::max(1, b->grid / G);
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof cfg);
-  cfg.gridDim = dim3(b->grid);
-  cfg.blockDim = dim3(256);
+  cfg.gridDim = dim3(G * cpg);
+  cfg.blockDim = dim3(kBatchThreads);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const BatchLattice* d = b->d_desc;
-  const int nl = b->n;
-  const int64_t tot = b->total_items;
+  const uint32_t* sw = b->d_sweep;
   cudaError_t e;
   switch (b->prec) {
-    case kF64: e = cudaLaunchKernelEx(&cfg, k_batch_sweep<kF64>, d, nl, tot, n, (const uint32_t*)b->d_sweep, hp, b->d_bar, b->timeout_ns); break;
-    case kF32: e = cudaLaunchKernelEx(&cfg, k_batch_sweep<kF32>, d, nl, tot, n, (const uint32_t*)b->d_sweep, hp, b->d_bar, b->timeout_ns); break;
-    default: e = cudaLaunchKernelEx(&cfg, k_batch_sweep<kF16Q>, d, nl, tot, n, (const uint32_t*)b->d_sweep, hp, b->d_bar, b->timeout_ns); break;
+    case kF64: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF64>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
+    case kF32: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF32>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
+    default: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF16Q>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
   }
-  if (e != cudaSuccess) return e;
-  count_launches(1);
-  return launch_add_u32(b->d_sweep, (uint32_t)n, st);
+  if (e == cudaSuccess) count_launches(1);
+  return e;
+}
+
+int check_ctl(su2_batch* b) {
+  int err = 0;
+  SU2_CU(cudaMemcpyAsync(&err, &b->d_ctl->err, sizeof err, cudaMemcpyDeviceToHost, b->stream));
+  SU2_CU(cudaStreamSynchronize(b->stream));
+  if (err) return fail(SU2_ETIMEOUT, "a group barrier of the batched sweep timed out; lattice contents are invalid");
+  return SU2_OK;
 }
 
 }  // namespace
@@ -250,23 +391,22 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   b->dims.assign(dims, dims + 4 * n);
   b->betas.assign(betas, betas + n);
   cudaGetDevice(&b->device);
-  // layout: per-lattice stores, descriptors, barrier, sweep counter, scratch, results
+  // layout: per-lattice stores, descriptors, plan, barriers, sweep counter, scratch, results
   std::vector<size_t> off(n);
   size_t o = 0;
-  int64_t items = 0;
   b->desc.resize(n);
   for (int i = 0; i < n; ++i) {
     b->desc[i].g = make_geom(dims + 4 * i);
     b->desc[i].beta = betas[i];
-    b->desc[i].item_begin = items;
-    items += b->desc[i].g.vh;
     off[i] = o;
     o = align256(o + 8 * (size_t)b->desc[i].g.vh * link_bytes(prec));
   }
-  if (items >= ((int64_t)1 << 40)) { delete b; return fail(SU2_EINVAL, "batch too large"); }
-  b->total_items = items;
+  b->links_bytes = o;
   const size_t o_desc = o; o = align256(o + n * sizeof(BatchLattice));
-  const size_t o_bar = o; o = align256(o + sizeof(BarrierState));
+  const size_t o_order = o; o = align256(o + n * sizeof(int));
+  const size_t o_plan = o; o = align256(o + kMaxGroups * sizeof(int2));
+  const size_t o_bars = o; o = align256(o + kMaxGroups * sizeof(GroupBarrier));
+  const size_t o_ctl = o; o = align256(o + sizeof(BatchCtl));
   const size_t o_sweep = o; o = align256(o + 64);
   const size_t o_part = o; o = align256(o + kScratchPartials * sizeof(double));
   const size_t o_cnt = o; o = align256(o + 64 * sizeof(unsigned int));
@@ -281,7 +421,10 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   char* base = (char*)b->base;
   for (int i = 0; i < n; ++i) b->desc[i].links = base + off[i];
   b->d_desc = (BatchLattice*)(base + o_desc);
-  b->d_bar = (BarrierState*)(base + o_bar);
+  b->d_order = (int*)(base + o_order);
+  b->d_plan = (int2*)(base + o_plan);
+  b->d_bars = (GroupBarrier*)(base + o_bars);
+  b->d_ctl = (BatchCtl*)(base + o_ctl);
   b->d_sweep = (uint32_t*)(base + o_sweep);
   b->scratch.partials = (double*)(base + o_part);
   b->scratch.counter = (unsigned int*)(base + o_cnt);
@@ -296,16 +439,17 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   SU2_CU_CLEAN(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaMallocHost(&b->h_results, 3 * (size_t)n * sizeof(double)), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaMemcpyAsync(b->d_desc, b->desc.data(), n * sizeof(BatchLattice), cudaMemcpyHostToDevice, b->stream), su2_batch_destroy(b));
-  BarrierState bs;
-  std::memset(&bs, 0, sizeof bs);
-  // Fault injection for the timeout path, host-side switch: the barrier then
-  // waits for one arrival that never comes and every wait runs out.
+  SU2_CU_CLEAN(cudaMemsetAsync(b->d_bars, 0, kMaxGroups * sizeof(GroupBarrier), b->stream), su2_batch_destroy(b));
+  BatchCtl ctl;
+  std::memset(&ctl, 0, sizeof ctl);
+  // Fault injection for the timeout path, host-side switch: every barrier
+  // then waits for one arrival that never comes and every wait runs out.
   const char* fault = std::getenv("SU2_FAULT");
   if (fault && std::strcmp(fault, "barrier") == 0) {
-    bs.extra = 1;
+    ctl.extra = 1;
     b->timeout_ns = 20000000ull;
   }
-  SU2_CU_CLEAN(cudaMemcpyAsync(b->d_bar, &bs, sizeof bs, cudaMemcpyHostToDevice, b->stream), su2_batch_destroy(b));
+  SU2_CU_CLEAN(cudaMemcpyAsync(b->d_ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, b->stream), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaMemsetAsync(b->d_sweep, 0, 64, b->stream), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaMemsetAsync(b->scratch.counter, 0, 64 * sizeof(unsigned int), b->stream), su2_batch_destroy(b));
   const PhiloxKey key = batch_key(b);
@@ -313,6 +457,11 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
     SU2_CU_CLEAN(launch_init(lview(b, i), start, key, (uint32_t)i << 2, b->stream), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaStreamSynchronize(b->stream), su2_batch_destroy(b));
   b->grid = batch_grid(prec);
+  int rc = set_groups(b, default_groups(b));
+  if (rc) {
+    su2_batch_destroy(b);
+    return rc;
+  }
   *out = b;
   return SU2_OK;
 }
@@ -341,6 +490,22 @@ extern "C" int su2_batch_set_options(su2_batch* b, int max_tries, int sampler) {
   return SU2_OK;
 }
 
+extern "C" int su2_batch_set_groups(su2_batch* b, int groups) {
+  clear_error();
+  if (!b) return fail(SU2_EINVAL, "handle is NULL");
+  if (groups < 1 || groups > b->n || groups > b->grid || groups > kMaxGroups)
+    return fail(SU2_EINVAL, "groups must be in 1..min(lattices, co-resident CTAs, %d)", kMaxGroups);
+  DeviceGuard dg(b->device);
+  return set_groups(b, groups);
+}
+
+extern "C" int su2_batch_groups(su2_batch* b, int* groups) {
+  clear_error();
+  if (!b || !groups) return fail(SU2_EINVAL, "NULL argument");
+  *groups = b->groups;
+  return SU2_OK;
+}
+
 extern "C" int su2_batch_sweep(su2_batch* b, int n) {
   clear_error();
   if (!b) return fail(SU2_EINVAL, "handle is NULL");
@@ -353,7 +518,8 @@ extern "C" int su2_batch_sweep(su2_batch* b, int n) {
     cudaGraph_t graph;
     CaptureScope no_count;
     SU2_CU(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_batch_sweep(b, n, b->cap_stream);
+    cudaError_t e = launch_groups(b, b->d_desc, n, b->cap_stream);
+    if (e == cudaSuccess) e = launch_add_u32(b->d_sweep, (uint32_t)n, b->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (e2 == cudaSuccess) cudaGraphDestroy(graph);
@@ -370,12 +536,69 @@ extern "C" int su2_batch_sweep(su2_batch* b, int n) {
   SU2_CU(cudaGraphLaunch(b->graph, b->stream));
   count_launches(2);
   b->sweep += (uint64_t)n;
-  // The barrier flag is checked on the next synchronising call; check it
-  // here too so a timed-out sweep is reported by the call that ran it.
-  int err = 0;
-  SU2_CU(cudaMemcpyAsync(&err, &b->d_bar->err, sizeof err, cudaMemcpyDeviceToHost, b->stream));
-  SU2_CU(cudaStreamSynchronize(b->stream));
-  if (err) return fail(SU2_ETIMEOUT, "a grid barrier of the batched sweep timed out; lattice contents are invalid");
+  // a timed-out barrier is reported by the call that ran it
+  return check_ctl(b);
+}
+
+extern "C" int su2_batch_tune(su2_batch* b, int sweeps, int* groups) {
+  clear_error();
+  if (!b) return fail(SU2_EINVAL, "handle is NULL");
+  if (sweeps < 1) return fail(SU2_EINVAL, "sweeps must be >= 1");
+  DeviceGuard dg(b->device);
+  // a scratch copy of the links, so the chain itself is not advanced
+  void* copy = nullptr;
+  SU2_CU(cudaMallocAsync(&copy, b->links_bytes + align256(b->n * sizeof(BatchLattice)), b->stream));
+  BatchLattice* d_desc_copy = (BatchLattice*)((char*)copy + b->links_bytes);
+  std::vector<BatchLattice> dc = b->desc;
+  for (int i = 0; i < b->n; ++i) dc[i].links = (char*)copy + ((char*)b->desc[i].links - (char*)b->base);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(copy, b->stream);
+    cudaStreamSynchronize(b->stream);
+  };
+  cudaError_t e = cudaMemcpyAsync(copy, b->base, b->links_bytes, cudaMemcpyDeviceToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_desc_copy, dc.data(), b->n * sizeof(BatchLattice), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(SU2_ECUDA, "tuning set-up failed: %s", cudaGetErrorString(e));
+  }
+  const int original = b->groups;
+  std::vector<int> cand;
+  for (int G : {1, 2, 4, 8, 12, 16, 24, 32, 40, 48, 64, 96, 128}) cand.push_back(G);
+  cand.push_back(default_groups(b));
+  cand.push_back(b->n);
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  int best = original;
+  float best_ms = 1e30f;
+  for (int G : cand) {
+    if (G < 1 || G > b->n || G > b->grid || G > kMaxGroups) continue;
+    int rc = set_groups(b, G);
+    if (rc) { cleanup(); return rc; }
+    e = launch_groups(b, d_desc_copy, sweeps, b->stream);  // warm the schedule
+    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+    if (e == cudaSuccess) e = launch_groups(b, d_desc_copy, sweeps, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      cleanup();
+      set_groups(b, original);
+      return fail(SU2_ECUDA, "tuning launch failed: %s", cudaGetErrorString(e));
+    }
+    int rc2 = check_ctl(b);
+    if (rc2) { cleanup(); return rc2; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = G; }
+  }
+  cleanup();
+  int rc = set_groups(b, best);
+  if (rc) return rc;
+  if (groups) *groups = best;
   return SU2_OK;
 }
 

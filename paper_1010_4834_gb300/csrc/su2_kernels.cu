@@ -389,6 +389,51 @@ __device__ __forceinline__ typename Real<P>::T plaq(const Links<P>& L, int q, co
   return qdot(a, b);
 }
 
+// The sixteen links one site's six plaquettes use: its own four and, for each
+// direction mu, the three U_nu(x + mu) with nu != mu.
+template <int P> struct PlaqLinks { Quat<typename Real<P>::T> u[4], n[4][3]; };
+
+template <int P>
+__device__ __forceinline__ void plaq_load(const Links<P>& L, const Geom& g, int s, PlaqLinks<P>& k, int& p) {
+  const Site x = site_from_index(g, (uint32_t)s);
+  p = parity(x);
+  const int q = p ^ 1;
+  const int h = s >> 1;
+  const int hm[4] = {hidx(g, shifted<0, +1>(g, x)), hidx(g, shifted<1, +1>(g, x)), hidx(g, shifted<2, +1>(g, x)),
+                     hidx(g, shifted<3, +1>(g, x))};
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) k.u[mu] = L.ld(2 * mu + p, h);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int nu = j < mu ? j : j + 1;
+      k.n[mu][j] = L.ld(2 * nu + q, hm[mu]);
+    }
+  }
+}
+
+// U_nu(x + mu) among the loaded links.
+template <int P>
+__device__ __forceinline__ const Quat<typename Real<P>::T>& plaq_nb(const PlaqLinks<P>& k, int mu, int nu) {
+  return k.n[mu][nu < mu ? nu : nu - 1];
+}
+
+template <int P>
+__device__ __forceinline__ void plaq_sums(const PlaqLinks<P>& k, typename Real<P>::T& ss, typename Real<P>::T& ts) {
+  using R = typename Real<P>::T;
+  ss = R(0);
+  ts = R(0);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+    for (int nu = mu + 1; nu < 4; ++nu) {
+      const R v = qdot(qmul(k.u[mu], plaq_nb<P>(k, mu, nu)), qmul(k.u[nu], plaq_nb<P>(k, nu, mu)));
+      if (nu == 3) ts += v; else ss += v;
+    }
+  }
+}
+
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_plaquette(Links<P> L, Geom g, double* partials,
                                                         unsigned int* counter, double* out) {
@@ -396,21 +441,15 @@ __global__ void __launch_bounds__(kThreads) k_plaquette(Links<P> L, Geom g, doub
   Acc<R> sp, tm;
   const int V = (int)(2 * g.vh);
   const int stride = gridDim.x * blockDim.x;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
-    const Site x = site_from_index(g, (uint32_t)s);
-    const int p = parity(x), q = p ^ 1;
-    const int h = s >> 1;
-    const Quat<R> u0 = L.ld(0 + p, h), u1 = L.ld(2 + p, h), u2 = L.ld(4 + p, h), u3 = L.ld(6 + p, h);
-    const int h0 = hidx(g, shifted<0, +1>(g, x));
-    const int h1 = hidx(g, shifted<1, +1>(g, x));
-    const int h2 = hidx(g, shifted<2, +1>(g, x));
-    const int h3 = hidx(g, shifted<3, +1>(g, x));
-    const R ssum = plaq<P>(L, q, u0, u1, 0, 1, h0, h1) + plaq<P>(L, q, u0, u2, 0, 2, h0, h2) +
-                   plaq<P>(L, q, u1, u2, 1, 2, h1, h2);
-    const R tsum = plaq<P>(L, q, u0, u3, 0, 3, h0, h3) + plaq<P>(L, q, u1, u3, 1, 3, h1, h3) +
-                   plaq<P>(L, q, u2, u3, 2, 3, h2, h3);
-    sp.add(ssum);
-    tm.add(tsum);
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; s < V; s += stride) {
+    PlaqLinks<P> k0;
+    int p0;
+    plaq_load<P>(L, g, s, k0, p0);
+    R ss0, ts0;
+    plaq_sums<P>(k0, ss0, ts0);
+    sp.add(ss0);
+    tm.add(ts0);
   }
   double v[2] = {sp.value(), tm.value()};
   if (block_partial<2>(v, partials, counter)) {

@@ -219,6 +219,22 @@ class Batch:
     def sweep(self, n=1):
         check(_lib.load().su2_batch_sweep(self._h, int(n)))
 
+    @property
+    def groups(self):
+        g = C.c_int()
+        check(_lib.load().su2_batch_groups(self._h, C.byref(g)))
+        return g.value
+
+    @groups.setter
+    def groups(self, g):
+        check(_lib.load().su2_batch_set_groups(self._h, int(g)))
+
+    def tune(self, sweeps=4):
+        """Pick the fastest group count on a scratch copy; returns it."""
+        g = C.c_int()
+        check(_lib.load().su2_batch_tune(self._h, int(sweeps), C.byref(g)))
+        return g.value
+
     def plaquette(self):
         out = np.empty((self.n, 3))
         check(_lib.load().su2_batch_plaquette(self._h, _dptr(out)))

@@ -296,6 +296,40 @@ def test_batched_sweep_parity(prec):
     b.close()
 
 
+def test_batched_result_is_independent_of_the_schedule():
+    dims = [(4, 4, 4, 4), (6, 4, 4, 2), (8, 8, 8, 8), (6, 6, 6, 4), (4, 4, 2, 8)]
+    betas = [2.0, 2.5, 2.7, 0.0, 2.2]
+    ref = None
+    for G in (1, 2, 3, 5):
+        b = Batch(dims, betas, seed=31, start="hot", prec="f32")
+        b.groups = G
+        assert b.groups == G
+        b.sweep(3)
+        links = [b.get_links(i) for i in range(len(dims))]
+        b.close()
+        if ref is None:
+            ref = links
+        else:
+            for a, c in zip(ref, links):
+                assert np.array_equal(a, c)
+
+
+def test_batched_tuner_keeps_the_chain():
+    dims = [(8, 8, 8, 8), (6, 6, 6, 6), (4, 4, 4, 4)]
+    a = Batch(dims, [2.3, 2.4, 2.5], seed=41, start="hot", prec="f32")
+    b = Batch(dims, [2.3, 2.4, 2.5], seed=41, start="hot", prec="f32")
+    g = a.tune(2)
+    assert 1 <= g <= 3 and a.groups == g
+    a.sweep(2)
+    b.sweep(2)
+    for i in range(3):
+        assert np.array_equal(a.get_links(i), b.get_links(i))
+    with pytest.raises(SU2Error):
+        a.groups = 4
+    a.close()
+    b.close()
+
+
 def test_batched_matches_single_lattice_chain():
     dims = [(4, 4, 4, 4), (6, 6, 6, 4)]
     b = Batch(dims, [2.2, 2.6], seed=21, start="hot", prec="f64")
