@@ -105,7 +105,8 @@ int su2_init(su2_lattice** h, const int dims[4], double beta, uint64_t seed, int
 /*
  * As su2_init, but all device memory comes from the caller: `dev_buf` is a
  * device pointer to `bytes` >= su2_required_bytes() bytes, 256-byte aligned,
- * which the caller keeps alive until su2_destroy.  SU2_ENOMEM if too small.
+ * which the caller keeps alive until su2_destroy.  SU2_ENOMEM if too small,
+ * SU2_EINVAL if NULL or not 256-byte aligned.
  */
 int su2_init_external(su2_lattice** h, const int dims[4], double beta, uint64_t seed, int start,
                       int prec, void* dev_buf, size_t bytes, void* cuda_stream);

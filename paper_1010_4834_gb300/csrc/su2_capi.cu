@@ -378,11 +378,19 @@ extern "C" int su2_sweep_measure(su2_lattice* h, int n, double* hist) {
   for (int c0 = 0; c0 < n; c0 += kHistSweeps) {
     const int m = n - c0 < kHistSweeps ? n - c0 : kHistSweeps;
     for (int i = 0; i < m; ++i) {
-      SU2_CU(enqueue_sweep(h, 0u, h->stream));
+      // the sweep's odd-parity substeps of mu = 1, 2, 3 also sum the
+      // plaquettes their links close (see k_heatbath), so the plaquette after
+      // the sweep needs no separate pass over the links
+      const HBParams hp = hb_params(h);
+      int nb[3] = {0, 0, 0};
+      for (int mu = 0; mu < 4; ++mu)
+        for (int p = 0; p < 2; ++p) {
+          double* meas = (mu >= 1 && p == 1) ? h->scratch.partials + (size_t)(mu - 1) * kMeasStride : nullptr;
+          SU2_CU(launch_heatbath(v, mu, p, h->d_sweep, 0u, hp, nullptr, h->stream, meas, meas ? &nb[mu - 1] : nullptr));
+        }
       SU2_CU(launch_add_u32(h->d_sweep, 1u, h->stream));
+      SU2_CU(launch_plaquette_from_sweep(h->scratch.partials, nb, 2 * v.g.vh, h->d_hist + 4 * i, h->stream));
       Scratch sp = h->scratch;
-      sp.out = h->d_hist + 4 * i;
-      SU2_CU(launch_plaquette(v, sp, h->stream));
       sp.out = h->d_hist + 4 * i + 3;
       SU2_CU(launch_polyakov(v, sp, h->stream));
     }

@@ -327,6 +327,11 @@ template <> struct Links<kF64> {
     q[0] = make_double2(v.w, v.x);
     q[1] = make_double2(v.y, v.z);
   }
+  // store v and return the value a later load of it returns
+  __device__ __forceinline__ Quat<double> put(int cls, int i, const Quat<double>& v) const {
+    st(cls, i, v);
+    return v;
+  }
 };
 
 template <> struct Links<kF32> {
@@ -343,6 +348,10 @@ template <> struct Links<kF32> {
   __device__ __forceinline__ void st(int cls, int i, const Quat<float>& v) const {
     p[cls * vh + i] = make_float4(v.w, v.x, v.y, v.z);
   }
+  __device__ __forceinline__ Quat<float> put(int cls, int i, const Quat<float>& v) const {
+    st(cls, i, v);
+    return v;
+  }
 };
 
 // binary16 quaternion, re-normalised in FP32 on every load.
@@ -357,13 +366,20 @@ template <> struct Links<kF16Q> {
     Quat<float> q = qmake<float>(lo.x, lo.y, hi.x, hi.y);
     return qscale(q, rsqrtf(qdot(q, q)));
   }
-  __device__ __forceinline__ void st(int cls, int i, const Quat<float>& v) const {
+  static __device__ __forceinline__ uint2 pack(const Quat<float>& v) {
     const __half2 lo = __floats2half2_rn(v.w, v.x);
     const __half2 hi = __floats2half2_rn(v.y, v.z);
     uint2 a;
     a.x = *reinterpret_cast<const uint32_t*>(&lo);
     a.y = *reinterpret_cast<const uint32_t*>(&hi);
+    return a;
+  }
+  __device__ __forceinline__ void st(int cls, int i, const Quat<float>& v) const { p[cls * vh + i] = pack(v); }
+  // the stored value as a later load sees it: rounded to binary16, re-normalised
+  __device__ __forceinline__ Quat<float> put(int cls, int i, const Quat<float>& v) const {
+    const uint2 a = pack(v);
     p[cls * vh + i] = a;
+    return unpack(a);
   }
 };
 
@@ -539,6 +555,27 @@ __device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P>& L, c
   if (MU != 1 && (NMASK & 2)) staple_term<P, MU, 1, NC>(L, g, x, h, h_pmu, p, s);
   if (MU != 2 && (NMASK & 4)) staple_term<P, MU, 2, NC>(L, g, x, h, h_pmu, p, s);
   if (MU != 3 && (NMASK & 8)) staple_term<P, MU, 3, NC>(L, g, x, h, h_pmu, p, s);
+  return s;
+}
+
+// The staple sum of all NU != MU, accumulated in the same order as staple(),
+// with `lower` set to the partial sum over NU < MU.  Tr(U_MU(x) lower^dagger)/2
+// is the sum of the plaquettes in the planes (NU, MU), NU < MU, that contain
+// the link (Section 2, Eq. 12).
+template <int P, int MU, bool NC>
+__device__ __forceinline__ Quat<typename Real<P>::T> staple_split(const Links<P>& L, const Geom& g, const Site& x,
+                                                                 int h, int p, Quat<typename Real<P>::T>& lower) {
+  using R = typename Real<P>::T;
+  Quat<R> s = qmake<R>(0, 0, 0, 0);
+  const int h_pmu = hidx(g, shifted<MU, +1>(g, x));
+  if (MU != 0) staple_term<P, MU, 0, NC>(L, g, x, h, h_pmu, p, s);
+  if (MU == 1) lower = s;
+  if (MU != 1) staple_term<P, MU, 1, NC>(L, g, x, h, h_pmu, p, s);
+  if (MU == 2) lower = s;
+  if (MU != 2) staple_term<P, MU, 2, NC>(L, g, x, h, h_pmu, p, s);
+  if (MU == 3) lower = s;
+  if (MU != 3) staple_term<P, MU, 3, NC>(L, g, x, h, h_pmu, p, s);
+  if (MU == 0) lower = qmake<R>(0, 0, 0, 0);
   return s;
 }
 

@@ -41,9 +41,17 @@ size_t scratch_bytes();
 // --- launches (all stream-ordered, return cudaGetLastError()) ------------
 cudaError_t launch_init(const LatticeView& v, int start, PhiloxKey key, uint32_t lattice_tag,
                         cudaStream_t st);
+// With `meas` (only for mu >= 1, parity 1) the substep also writes one
+// plaquette block sum per block to meas[0, *meas_blocks) (see k_heatbath).
 cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint32_t* sweep_base,
                             uint32_t sweep_off, const HBParams& hp, unsigned long long* stats,
-                            cudaStream_t st);
+                            cudaStream_t st, double* meas = nullptr, int* meas_blocks = nullptr);
+// Block sums of the three measuring substeps at meas + k * kMeasStride
+// (k = 0, 1, 2 for mu = 1, 2, 3; nb[k] blocks each) -> out[3] = plaquette
+// {all, spatial, space-time}.
+constexpr int kMeasStride = 8192;
+cudaError_t launch_plaquette_from_sweep(const double* meas, const int nb[3], int64_t volume, double* out,
+                                        cudaStream_t st);
 cudaError_t launch_overrelax(const LatticeView& v, int mu, int parity, cudaStream_t st);
 cudaError_t launch_plaquette(const LatticeView& v, const Scratch& s, cudaStream_t st);
 cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t st);

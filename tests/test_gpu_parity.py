@@ -406,12 +406,16 @@ def test_sweep_measure_restart_and_launch_count():
     b = Lattice(dims, 2.3, seed=5, start="hot", prec="f64")
     n0 = kernel_launches()
     hist = a.sweep_measure(6)
-    assert kernel_launches() - n0 == 6 * (8 + 1 + 2)      # 8 substeps, counter, plaquette, Polyakov
+    assert kernel_launches() - n0 == 6 * (8 + 1 + 2)      # 8 substeps, counter, plaquette sum, Polyakov
     ref = []
     for _ in range(6):
         b.sweep(1)
         ref.append(list(b.plaquette()) + [b.polyakov()])
-    np.testing.assert_array_equal(hist, np.array(ref))
+    ref = np.array(ref)
+    # the plaquette comes from the sweep's own staples: same sum, other order
+    np.testing.assert_allclose(hist[:, :3], ref[:, :3], rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(hist[:, 3], ref[:, 3])
+    np.testing.assert_array_equal(a.get_links(), b.get_links())
     assert a.sweep_count == 6
     a.restart("hot")
     assert a.sweep_count == 0
@@ -419,6 +423,51 @@ def test_sweep_measure_restart_and_launch_count():
     assert np.array_equal(a.get_links(), fresh.get_links())
     for lat in (a, b, fresh):
         lat.close()
+
+
+# The plaquette that sweep_measure takes from the odd-parity substeps of
+# mu = 1, 2, 3 against the plaquette kernel run after a plain sweep: every
+# branch of the update (first-trial accept, deferred trials, queue overflow,
+# capped link kept, Haar link at beta = 0, Creutz), each precision, a lattice
+# of several blocks with a ragged last one.  The measured sweeps must leave the
+# same links as plain ones.
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-14), ("f32", 3e-6), ("f16q", 3e-6)])
+@pytest.mark.parametrize("beta,max_tries,sampler", [
+    (2.3, 64, "kp"),      # mostly first-trial accepts, a few deferred
+    (0.4, 64, "kp"),      # low acceptance: many deferred
+    (2.3, 1, "kp"),       # capped links keep their old value
+    (0.0, 64, "kp"),      # alpha = 0: Haar links
+    (2.3, 64, "creutz"),
+])
+def test_sweep_plaquette_matches_plaquette_kernel(prec, tol, beta, max_tries, sampler):
+    dims = (8, 6, 4, 10)                 # V/2 = 960: four blocks, the last one partial
+    a = Lattice(dims, beta, seed=41, start="hot", prec=prec)
+    b = Lattice(dims, beta, seed=41, start="hot", prec=prec)
+    for lat in (a, b):
+        lat.set_options(max_tries=max_tries, sampler=sampler)
+    hist = a.sweep_measure(3)
+    for i in range(3):
+        b.sweep(1)
+        np.testing.assert_allclose(hist[i, :3], b.plaquette(), rtol=0, atol=tol)
+        assert hist[i, 3] == b.polyakov()
+    np.testing.assert_array_equal(a.get_links(), b.get_links())
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("beta", [2.5, 0.05])
+def test_sweep_plaquette_full_size_grid(beta):
+    # 32^4: the substeps run the full persistent grid, several iterations per
+    # block; at beta 0.05 most first trials fail, the block queues overflow
+    # and some links exhaust their trials
+    a = Lattice((32, 32, 32, 32), beta, seed=43, start="hot", prec="f32")
+    b = Lattice((32, 32, 32, 32), beta, seed=43, start="hot", prec="f32")
+    hist = a.sweep_measure(2)
+    b.sweep(2)
+    np.testing.assert_allclose(hist[-1, :3], b.plaquette(), rtol=0, atol=2e-6)
+    np.testing.assert_array_equal(a.get_links(), b.get_links())
+    a.close()
+    b.close()
 
 
 def test_work_is_ordered_on_the_torch_stream():
