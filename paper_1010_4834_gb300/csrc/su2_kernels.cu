@@ -930,6 +930,174 @@ __global__ void __launch_bounds__(kThreads) k_wilson_plane_final(const double* p
   }
 }
 
+// ---------------------------------------------------------------------------
+// Wilson loops, time-outer form.  In the (MU, time) plane with coordinates
+// (a, t), S_R(a, t) = U_MU(a, t) ... U_MU(a+R-1, t) and T_T(a, t) = U_t(a, t)
+// ... U_t(a, t+T-1), the loop of Eq. 18 at (a, t) is
+//   W = (1/2) Tr[S_R(a,t) T_T(a+R,t) S_R(a,t+T)^dag T_T(a,t)^dag]
+//     = (F . Q),  F = S_R(a,t) T_T(a+R,t),  Q = T_T(a,t) S_R(a,t+T).
+// A thread owns one site of a plane staged in shared memory and holds F for
+// RC consecutive R in registers.  Stepping T by one multiplies each F by one
+// time link and D = T_T(a,t) by one; Q is then rebuilt along R from D with
+// one spatial link per R.  That is two quaternion products and a dot product
+// per (R, T), where extending every line per (R, T) costs four to five.
+// blockIdx.y = (R chunk, T chunk); chunks after the first start from prefix
+// products.  Loop values go through a transposing warp reduction into the
+// block's shared accumulators; per-block sums go to `partials` in a fixed
+// layout for k_wilson_rt_final.
+// ---------------------------------------------------------------------------
+constexpr int kWrtT = 16;  // T values per chunk
+
+template <int P, int RC, int NTH>
+__global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, Geom g, int rmax, int tmax,
+                                                      int ntc, double* partials) {
+  using R = typename Real<P>::T;
+  static_assert(RC == 8 || RC == 16, "R chunk must be 8 or 16");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double acc[RC * kWrtT];
+  const int lane = threadIdx.x & 31;
+  const int rc = blockIdx.y / ntc, tc = blockIdx.y - (blockIdx.y / ntc) * ntc;
+  const int r0 = rc * RC, t0 = tc * kWrtT;
+  const int nR = min(RC, rmax - r0), nT = min(kWrtT, tmax - t0);
+  const int nt = g.n[3];
+  for (int i = threadIdx.x; i < RC * kWrtT; i += NTH) acc[i] = 0.0;
+  const int ntr0 = g.n[1] * g.n[2], ntr1 = g.n[0] * g.n[2], ntr2 = g.n[0] * g.n[1];
+  const int nplanes = ntr0 + ntr1 + ntr2;
+  for (int pl = blockIdx.x; pl < nplanes; pl += gridDim.x) {
+    const int mu = pl < ntr0 ? 0 : (pl < ntr0 + ntr1 ? 1 : 2);
+    const int tr = pl - (mu == 0 ? 0 : (mu == 1 ? ntr0 : ntr0 + ntr1));
+    const int nm = mu == 0 ? g.n[0] : (mu == 1 ? g.n[1] : g.n[2]);
+    const int np = nm * nt;
+    Quat<R>* us = reinterpret_cast<Quat<R>*>(smem_raw);   // us[a + nm t] = U_mu(a, t)
+    Quat<R>* ut = us + np;                                // ut[a + nm t] = U_t(a, t)
+    const int n1st = mu == 0 ? g.n[1] : g.n[0];
+    const int c1 = tr % n1st, c2 = tr / n1st;
+    __syncthreads();  // the previous plane's readers are done
+    for (int i = threadIdx.x; i < np; i += NTH) {
+      const int a = i % nm, t = i / nm;
+      Site y;
+      y.x0 = mu == 0 ? a : c1;
+      y.x1 = mu == 0 ? c1 : (mu == 1 ? a : c2);
+      y.x2 = mu == 2 ? a : c2;
+      y.x3 = t;
+      y.row = y.x1 + g.n[1] * (y.x2 + g.n[2] * y.x3);
+      const int h = hidx(g, y), par = parity(y);
+      us[i] = Ls.ld(2 * mu + par, h);
+      ut[i] = Lt.ld(6 + par, h);
+    }
+    __syncthreads();
+    for (int base = 0; base < np; base += NTH) {
+      const int i = base + threadIdx.x;
+      const bool valid = i < np;
+      const int a = valid ? i % nm : 0, t = valid ? i / nm : 0;
+      // F[k] = S_{r0+k+1}(a, t) T_{t0}(a+r0+k+1, t),  D = T_{t0}(a, t)
+      Quat<R> F[RC];
+      int ar = a;  // a + r0 (mod nm)
+      {
+        Quat<R> sp = qone<R>();
+        for (int k = 0; k < r0; ++k) { sp = qmul(sp, us[ar + nm * t]); ar = ar + 1 == nm ? 0 : ar + 1; }
+        int c = ar;
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+          sp = qmul(sp, us[c + nm * t]);
+          c = c + 1 == nm ? 0 : c + 1;
+          F[k] = sp;
+        }
+      }
+      const int ar1 = ar + 1 == nm ? 0 : ar + 1;  // a + r0 + 1
+      Quat<R> D = qone<R>();
+      int tt = t;                                   // t + T - 1 for the next T
+      for (int j = 0; j < t0; ++j) { D = qmul(D, ut[a + nm * tt]); tt = tt + 1 == nt ? 0 : tt + 1; }
+      if (t0 > 0) {
+        int c = ar1;
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+          int u = t;
+          for (int j = 0; j < t0; ++j) { F[k] = qmul(F[k], ut[c + nm * u]); u = u + 1 == nt ? 0 : u + 1; }
+          c = c + 1 == nm ? 0 : c + 1;
+        }
+      }
+      for (int j = 0; j < nT; ++j) {             // T = t0 + j + 1
+        const int row = nm * tt;
+        D = qmul(D, ut[a + row]);
+        {
+          int c = ar1;
+#pragma unroll
+          for (int k = 0; k < RC; ++k) {
+            F[k] = qmul(F[k], ut[c + row]);
+            c = c + 1 == nm ? 0 : c + 1;
+          }
+        }
+        tt = tt + 1 == nt ? 0 : tt + 1;           // t + T
+        const int rown = nm * tt;
+        Quat<R> Q = D;
+        int c = a;
+        for (int k = 0; k < r0; ++k) { Q = qmul(Q, us[c + rown]); c = c + 1 == nm ? 0 : c + 1; }
+        R val[RC];
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+          Q = qmul(Q, us[c + rown]);
+          c = c + 1 == nm ? 0 : c + 1;
+          val[k] = (valid && k < nR) ? qdot(F[k], Q) : R(0);
+        }
+        int nv = RC, lo = 0;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+          if (nv > 1) {
+            const bool upper = (lane & off) != 0;
+            const int half = nv / 2;
+#pragma unroll
+            for (int k = 0; k < RC / 2; ++k) {
+              if (k < half) {
+                const R send = upper ? val[k] : val[k + half];
+                const R keep = upper ? val[k + half] : val[k];
+                val[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+              }
+            }
+            if (upper) lo += half;
+            nv = half;
+          } else {
+            val[0] += __shfl_xor_sync(0xffffffffu, val[0], off);
+          }
+        }
+        if ((lane & (32 / RC - 1)) == 0 && lo < nR) atomicAdd(&acc[lo * kWrtT + j], (double)val[0]);
+      }
+    }
+  }
+  __syncthreads();
+  const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  for (int i = threadIdx.x; i < RC * kWrtT; i += NTH) partials[bid * (RC * kWrtT) + i] = acc[i];
+}
+
+// out[(R-1) tmax + (T-1)] from k_wilson_rt's per-block sums: one block per
+// output adds the gx blocks of its (R chunk, T chunk) in a fixed order.
+template <int RC>
+__global__ void __launch_bounds__(kThreads) k_wilson_rt_final(const double* partials, int gx, int ntc, int tmax,
+                                                              double inv, double* out) {
+  __shared__ double ss[kThreads / 32], sc[kThreads / 32];
+  const int o = blockIdx.x;
+  const int r = o / tmax, t = o % tmax;
+  const int y = (r / RC) * ntc + t / kWrtT;
+  const int slot = (r % RC) * kWrtT + t % kWrtT;
+  KSum a;
+  for (int bx = threadIdx.x; bx < gx; bx += blockDim.x)
+    a.add(__ldcg(partials + ((size_t)y * gx + bx) * (RC * kWrtT) + slot));
+  a = warp_ksum(a);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { ss[warp] = a.s; sc[warp] = a.c; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    KSum tot;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      KSum q;
+      q.s = ss[w];
+      q.c = sc[w];
+      tot = ksum_combine(tot, q);
+    }
+    out[o] = tot.value() * inv;
+  }
+}
+
 // out[(R-1) tmax + (T-1)]: one block per output adds the per-block sums of the
 // three directions and all x-blocks of T's chunk, in a fixed order.
 template <int TC>
@@ -1168,9 +1336,76 @@ static cudaError_t launch_wilson_plane(const LatticeView& v, const void* spatial
   return cudaGetLastError();
 }
 
+#ifndef SU2_WILSON_RT
+#define SU2_WILSON_RT 1
+#endif
+constexpr int kWilsonRtThreads = 512;
+
+template <int P, int RC>
+static cudaError_t launch_wilson_rt_rc(const LatticeView& v, const void* spatial, int rmax, int tmax, int smem,
+                                       const Scratch& s, cudaStream_t st) {
+  constexpr int NTH = kWilsonRtThreads;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_wilson_rt<P, RC, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kWilsonPlaneSmemMax);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson_rt<P, RC, NTH>, NTH, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int nrc = (rmax + RC - 1) / RC, ntc = (tmax + kWrtT - 1) / kWrtT;
+  const int nchunks = nrc * ntc;
+  const int nplanes = v.g.n[1] * v.g.n[2] + v.g.n[0] * v.g.n[2] + v.g.n[0] * v.g.n[1];
+  int64_t gx = ((int64_t)device_info().sms * per_sm + nchunks - 1) / nchunks;
+  if (gx > nplanes) gx = nplanes;
+  const int64_t cap = (int64_t)kScratchPartials / (RC * kWrtT) / nchunks;
+  if (gx > cap) gx = cap;
+  if (gx < 1) gx = 1;
+  auto Lt = links_of<P>(v.links, v.g.vh);
+  auto Ls = links_of<P>(const_cast<void*>(spatial), v.g.vh);
+  k_wilson_rt<P, RC, NTH><<<dim3((unsigned)gx, nchunks), NTH, smem, st>>>(Ls, Lt, v.g, rmax, tmax, ntc, s.partials);
+  count_launches(1);
+  const int64_t V = 2 * v.g.vh;
+  k_wilson_rt_final<RC><<<rmax * tmax, kThreads, 0, st>>>(s.partials, (int)gx, ntc, tmax, 1.0 / (3.0 * (double)V),
+                                                          s.out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// The time-outer plane kernel, where a plane's two link planes fit in shared
+// memory; *used = false otherwise.
+template <int P>
+static cudaError_t launch_wilson_rt(const LatticeView& v, const void* spatial, int rmax, int tmax,
+                                    const Scratch& s, cudaStream_t st, bool* used) {
+  using R = typename Real<P>::T;
+  *used = false;
+  if constexpr (P == kF64) {
+    return cudaSuccess;  // FP64 planes take the older plane kernel (half the links per plane fit)
+  } else {
+  if (!SU2_WILSON_RT) return cudaSuccess;
+  const int nmax = v.g.n[0] > v.g.n[1] ? (v.g.n[0] > v.g.n[2] ? v.g.n[0] : v.g.n[2])
+                                       : (v.g.n[1] > v.g.n[2] ? v.g.n[1] : v.g.n[2]);
+  const int smem = 2 * nmax * v.g.n[3] * (int)sizeof(Quat<R>);
+  if (smem > kWilsonPlaneSmemMax) return cudaSuccess;
+  *used = true;
+  if (rmax <= 8) return launch_wilson_rt_rc<P, 8>(v, spatial, rmax, tmax, smem, s, st);
+  return launch_wilson_rt_rc<P, 16>(v, spatial, rmax, tmax, smem, s, st);
+  }
+}
+
 cudaError_t launch_wilson(const LatticeView& v, const void* spatial, int rmax, int tmax,
                           const Scratch& s, cudaStream_t st) {
   if (rmax < 1 || rmax > kWilsonMaxR || tmax < 1) return cudaErrorInvalidValue;
+  {
+    bool used = false;
+    cudaError_t e = cudaSuccess;
+    SU2_DISPATCH(v.prec, { e = launch_wilson_rt<P>(v, spatial, rmax, tmax, s, st, &used); });
+    if (e != cudaSuccess || used) return e;
+  }
   {
     bool used = false;
     cudaError_t e = cudaSuccess;

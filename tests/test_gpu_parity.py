@@ -188,6 +188,42 @@ def test_measurements_on_thermalised_configuration():
     lat.close()
 
 
+# Wilson loops across the kernels' chunk boundaries: R beyond one register
+# chunk (R = 17 needs a second chunk that starts from prefix products), a
+# partly used 16-wide R chunk, T beyond one 16-wide T chunk, and planes with
+# fewer than 32 sites per row (loops wrap several times around a row).
+_WILSON_REF = {}
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16q", "f64"])
+@pytest.mark.parametrize("dims,rmax,tmax", [((18, 18, 18, 4), 17, 4), ((12, 12, 12, 4), 12, 4),
+                                            ((4, 4, 4, 18), 4, 18), ((6, 10, 8, 6), 6, 6)])
+def test_wilson_loops_across_chunks(dims, rmax, tmax, prec):
+    U = inputs.random_field(dims, 23)
+    ref = as_stored(U, prec)
+    key = (dims, rmax, tmax, prec)
+    if key not in _WILSON_REF:
+        _WILSON_REF[key] = oracle.wilson_loops(list(dims), ref, rmax, tmax)
+    lat = Lattice(dims, 2.0, prec=prec)
+    lat.set_links(U)
+    np.testing.assert_allclose(lat.wilson_loops(rmax, tmax), _WILSON_REF[key], atol=MTOL[prec] * 5, rtol=0)
+    lat.close()
+
+
+def test_wilson_loops_both_chunkings_fp32_against_fp64_kernel():
+    # R and T both past their first chunk at once: the FP32 time-outer kernel
+    # against the FP64 kernels (pinned to the oracle above) on one field
+    dims = (18, 18, 18, 18)
+    U = inputs.random_field(dims, 29)
+    a = Lattice(dims, 2.0, prec="f32")
+    b = Lattice(dims, 2.0, prec="f64")
+    a.set_links(U)
+    b.set_links(as_stored(U, "f32"))
+    np.testing.assert_allclose(a.wilson_loops(17, 17), b.wilson_loops(17, 17), atol=1e-5, rtol=0)
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("n,alpha", [(0, 0.7), (1, 0.7), (3, 0.444), (25, 0.7)])
 def test_ape_and_smeared_wilson(prec, n, alpha):
