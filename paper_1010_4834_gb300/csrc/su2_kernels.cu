@@ -595,38 +595,66 @@ __global__ void __launch_bounds__(kThreads) k_polyakov(Links<P> L, Geom g, doubl
 // ---------------------------------------------------------------------------
 // APE smearing step (Section 2, Eq. 19), Jacobi: spatial link (x, mu) ->
 // P[(1-alpha) U + (alpha/4) (four spatial staples)], P = normalisation; a sum
-// with vanishing norm keeps U.  blockIdx.y = mu in 0..2.
+// with vanishing norm keeps U.
+//
+// One thread per site updates all three spatial links.  For a pair mu < nu
+// the two forward staple terms share one product: with
+// A = U_nu(x+mu) U_mu(x+nu)^dag, link mu gets U_nu(x) A^dag and link nu gets
+// U_mu(x) A.  Per site that is 27 link loads and 21 products instead of 39
+// and 24 for three independent link updates, and one site decode instead of
+// three.  Each link's staple terms are added nu ascending, forward then
+// backward.  blockIdx.y = parity.
 // ---------------------------------------------------------------------------
-template <int P, int MU>
-__device__ __forceinline__ void ape_site(const Links<P>& src, const Links<P>& dst, const Geom& g, int s,
-                                         typename Real<P>::T c0, typename Real<P>::T c1) {
+template <int P, int MU, int NU>
+__device__ __forceinline__ void ape_pair(const Links<P>& L, const Geom& g, const Site& x, int p,
+                                         const Quat<typename Real<P>::T>& umu, const Quat<typename Real<P>::T>& unu,
+                                         Quat<typename Real<P>::T>& smu, Quat<typename Real<P>::T>& snu) {
   using R = typename Real<P>::T;
-  using M = Math<R>;
-  const Site x = site_from_index(g, (uint32_t)s);
-  const int p = parity(x);
-  const int h = s >> 1;
-  const Quat<R> sig = staple<P, MU, 0x7, true>(src, g, x, h, p);
-  const Quat<R> u = src.ld(2 * MU + p, h);
-  const Quat<R> q = qmake<R>(c0 * u.w + c1 * sig.w, c0 * u.x + c1 * sig.x, c0 * u.y + c1 * sig.y,
-                             c0 * u.z + c1 * sig.z);
-  const R n2 = qdot(q, q);
-  dst.st(2 * MU + p, h, n2 >= M::kTiny ? qscale(q, M::rsqrt(n2)) : u);
+  const int q = p ^ 1;
+  const Quat<R> a = qmul_nd(L.ld(2 * NU + q, hidx(g, shifted<MU, +1>(g, x))), L.ld(2 * MU + q, hidx(g, shifted<NU, +1>(g, x))));
+  const Site xn = shifted<NU, -1>(g, x);   // x - nu
+  const Site xm = shifted<MU, -1>(g, x);   // x - mu
+  const int hn = hidx(g, xn), hm = hidx(g, xm);
+  // link mu, term nu: forward U_nu(x) A^dag, backward U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+  qacc_mul_nd(smu, unu, a);
+  qacc_mul(smu, qmul_dn(L.ld(2 * NU + q, hn), L.ld(2 * MU + q, hn)), L.ld(2 * NU + p, hidx(g, shifted<MU, +1>(g, xn))));
+  // link nu, term mu: forward U_mu(x) A, backward U_mu(x-mu)^dag U_nu(x-mu) U_mu(x-mu+nu)
+  qacc_mul(snu, umu, a);
+  qacc_mul(snu, qmul_dn(L.ld(2 * MU + q, hm), L.ld(2 * NU + q, hm)), L.ld(2 * MU + p, hidx(g, shifted<NU, +1>(g, xm))));
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads, Occ<P>::hb) k_ape(Links<P> src, Links<P> dst, Geom g,
-                                                              double alpha_d) {
+__device__ __forceinline__ void ape_store(const Links<P>& dst, int cls, int h, const Quat<typename Real<P>::T>& u,
+                                          const Quat<typename Real<P>::T>& sig, typename Real<P>::T c0,
+                                          typename Real<P>::T c1) {
+  using R = typename Real<P>::T;
+  const Quat<R> q = qmake<R>(c0 * u.w + c1 * sig.w, c0 * u.x + c1 * sig.x, c0 * u.y + c1 * sig.y,
+                             c0 * u.z + c1 * sig.z);
+  const R n2 = qdot(q, q);
+  dst.st(cls, h, n2 >= Math<R>::kTiny ? qscale(q, Math<R>::rsqrt(n2)) : u);
+}
+
+#ifndef SU2_APE3_MINB
+#define SU2_APE3_MINB 3
+#endif
+template <int P>
+__global__ void __launch_bounds__(kThreads, P == kF64 ? 2 : SU2_APE3_MINB) k_ape(Links<P> src, Links<P> dst, Geom g, double alpha_d) {
   using R = typename Real<P>::T;
   const R alpha = (R)alpha_d;
   const R c0 = R(1) - alpha, c1 = R(0.25) * alpha;
-  const int V = (int)(2 * g.vh);
+  const int p = blockIdx.y;
+  const int vh = (int)g.vh;
   const int stride = gridDim.x * blockDim.x;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
-    switch (blockIdx.y) {
-      case 0: ape_site<P, 0>(src, dst, g, s, c0, c1); break;
-      case 1: ape_site<P, 1>(src, dst, g, s, c0, c1); break;
-      default: ape_site<P, 2>(src, dst, g, s, c0, c1); break;
-    }
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < vh; h += stride) {
+    const Site x = site_from_half(g, (uint32_t)h, p);
+    const Quat<R> u0 = src.ld(0 + p, h), u1 = src.ld(2 + p, h), u2 = src.ld(4 + p, h);
+    Quat<R> s0 = qmake<R>(0, 0, 0, 0), s1 = s0, s2 = s0;
+    ape_pair<P, 0, 1>(src, g, x, p, u0, u1, s0, s1);
+    ape_pair<P, 0, 2>(src, g, x, p, u0, u2, s0, s2);
+    ape_pair<P, 1, 2>(src, g, x, p, u1, u2, s1, s2);
+    ape_store<P>(dst, 0 + p, h, u0, s0, c0, c1);
+    ape_store<P>(dst, 2 + p, h, u1, s1, c0, c1);
+    ape_store<P>(dst, 4 + p, h, u2, s2, c0, c1);
   }
 }
 
@@ -942,25 +970,31 @@ __global__ void __launch_bounds__(kThreads) k_wilson_plane_final(const double* p
 // one spatial link per R.  That is two quaternion products and a dot product
 // per (R, T), where extending every line per (R, T) costs four to five.
 // blockIdx.y = (R chunk, T chunk); chunks after the first start from prefix
-// products.  Loop values go through a transposing warp reduction into the
-// block's shared accumulators; per-block sums go to `partials` in a fixed
-// layout for k_wilson_rt_final.
+// products.  Plane rows are stored with `pad` extra columns repeating the
+// first ones, so the lines along MU need no periodic wrap test.  Loop values
+// go through a transposing warp reduction into per-warp FP32 sums of the
+// plane, which are folded into the block's FP64 totals after each plane in a
+// fixed order (no atomics); per-block sums go to `partials` in a fixed layout
+// for k_wilson_rt_final.
 // ---------------------------------------------------------------------------
 constexpr int kWrtT = 16;  // T values per chunk
 
 template <int P, int RC, int NTH>
 __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, Geom g, int rmax, int tmax,
-                                                      int ntc, double* partials) {
+                                                      int ntc, int pad, double* partials) {
   using R = typename Real<P>::T;
   static_assert(RC == 8 || RC == 16, "R chunk must be 8 or 16");
+  constexpr int NS = RC * kWrtT;  // (R, T) slots of one chunk
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double acc[RC * kWrtT];
-  const int lane = threadIdx.x & 31;
+  __shared__ double acc[NS];               // block totals; slot k belongs to thread k
+  __shared__ float wacc[NTH / 32][NS];     // one plane's sums per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rc = blockIdx.y / ntc, tc = blockIdx.y - (blockIdx.y / ntc) * ntc;
   const int r0 = rc * RC, t0 = tc * kWrtT;
   const int nR = min(RC, rmax - r0), nT = min(kWrtT, tmax - t0);
   const int nt = g.n[3];
-  for (int i = threadIdx.x; i < RC * kWrtT; i += NTH) acc[i] = 0.0;
+  for (int i = threadIdx.x; i < NS; i += NTH) acc[i] = 0.0;
+  for (int i = threadIdx.x; i < (NTH / 32) * NS; i += NTH) (&wacc[0][0])[i] = 0.f;
   const int ntr0 = g.n[1] * g.n[2], ntr1 = g.n[0] * g.n[2], ntr2 = g.n[0] * g.n[1];
   const int nplanes = ntr0 + ntr1 + ntr2;
   for (int pl = blockIdx.x; pl < nplanes; pl += gridDim.x) {
@@ -968,13 +1002,17 @@ __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, 
     const int tr = pl - (mu == 0 ? 0 : (mu == 1 ? ntr0 : ntr0 + ntr1));
     const int nm = mu == 0 ? g.n[0] : (mu == 1 ? g.n[1] : g.n[2]);
     const int np = nm * nt;
-    Quat<R>* us = reinterpret_cast<Quat<R>*>(smem_raw);   // us[a + nm t] = U_mu(a, t)
-    Quat<R>* ut = us + np;                                // ut[a + nm t] = U_t(a, t)
+    // rows of W = nm + pad columns: column c holds plane column c mod nm, so
+    // every line a, a+1, ..., a + pad - 1 is read without a wrap test
+    const int W = nm + pad;
+    Quat<R>* us = reinterpret_cast<Quat<R>*>(smem_raw);   // us[c + W t] = U_mu(c mod nm, t)
+    Quat<R>* ut = us + W * nt;                            // ut[c + W t] = U_t(c mod nm, t)
     const int n1st = mu == 0 ? g.n[1] : g.n[0];
     const int c1 = tr % n1st, c2 = tr / n1st;
-    __syncthreads();  // the previous plane's readers are done
-    for (int i = threadIdx.x; i < np; i += NTH) {
-      const int a = i % nm, t = i / nm;
+    __syncthreads();  // the previous plane's readers and the warp-sum fold are done
+    for (int i = threadIdx.x; i < W * nt; i += NTH) {
+      const int c = i % W, t = i / W;
+      const int a = c % nm;
       Site y;
       y.x0 = mu == 0 ? a : c1;
       y.x1 = mu == 0 ? c1 : (mu == 1 ? a : c2);
@@ -992,52 +1030,42 @@ __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, 
       const int a = valid ? i % nm : 0, t = valid ? i / nm : 0;
       // F[k] = S_{r0+k+1}(a, t) T_{t0}(a+r0+k+1, t),  D = T_{t0}(a, t)
       Quat<R> F[RC];
-      int ar = a;  // a + r0 (mod nm)
       {
+        const Quat<R>* row = us + a + W * t;
         Quat<R> sp = qone<R>();
-        for (int k = 0; k < r0; ++k) { sp = qmul(sp, us[ar + nm * t]); ar = ar + 1 == nm ? 0 : ar + 1; }
-        int c = ar;
+        for (int k = 0; k < r0; ++k) sp = qmul(sp, row[k]);
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
-          sp = qmul(sp, us[c + nm * t]);
-          c = c + 1 == nm ? 0 : c + 1;
+          sp = qmul(sp, row[r0 + k]);
           F[k] = sp;
         }
       }
-      const int ar1 = ar + 1 == nm ? 0 : ar + 1;  // a + r0 + 1
       Quat<R> D = qone<R>();
       int tt = t;                                   // t + T - 1 for the next T
-      for (int j = 0; j < t0; ++j) { D = qmul(D, ut[a + nm * tt]); tt = tt + 1 == nt ? 0 : tt + 1; }
-      if (t0 > 0) {
-        int c = ar1;
+      for (int j = 0; j < t0; ++j) {
+        D = qmul(D, ut[a + W * tt]);
+        if (t0 > 0) {
+          const Quat<R>* row = ut + a + r0 + 1 + W * tt;
 #pragma unroll
-        for (int k = 0; k < RC; ++k) {
-          int u = t;
-          for (int j = 0; j < t0; ++j) { F[k] = qmul(F[k], ut[c + nm * u]); u = u + 1 == nt ? 0 : u + 1; }
-          c = c + 1 == nm ? 0 : c + 1;
+          for (int k = 0; k < RC; ++k) F[k] = qmul(F[k], row[k]);
         }
+        tt = tt + 1 == nt ? 0 : tt + 1;
       }
       for (int j = 0; j < nT; ++j) {             // T = t0 + j + 1
-        const int row = nm * tt;
-        D = qmul(D, ut[a + row]);
+        D = qmul(D, ut[a + W * tt]);
         {
-          int c = ar1;
+          const Quat<R>* row = ut + a + r0 + 1 + W * tt;
 #pragma unroll
-          for (int k = 0; k < RC; ++k) {
-            F[k] = qmul(F[k], ut[c + row]);
-            c = c + 1 == nm ? 0 : c + 1;
-          }
+          for (int k = 0; k < RC; ++k) F[k] = qmul(F[k], row[k]);
         }
         tt = tt + 1 == nt ? 0 : tt + 1;           // t + T
-        const int rown = nm * tt;
+        const Quat<R>* row = us + a + W * tt;
         Quat<R> Q = D;
-        int c = a;
-        for (int k = 0; k < r0; ++k) { Q = qmul(Q, us[c + rown]); c = c + 1 == nm ? 0 : c + 1; }
+        for (int k = 0; k < r0; ++k) Q = qmul(Q, row[k]);
         R val[RC];
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
-          Q = qmul(Q, us[c + rown]);
-          c = c + 1 == nm ? 0 : c + 1;
+          Q = qmul(Q, row[r0 + k]);
           val[k] = (valid && k < nR) ? qdot(F[k], Q) : R(0);
         }
         int nv = RC, lo = 0;
@@ -1060,13 +1088,25 @@ __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, 
             val[0] += __shfl_xor_sync(0xffffffffu, val[0], off);
           }
         }
-        if ((lane & (32 / RC - 1)) == 0 && lo < nR) atomicAdd(&acc[lo * kWrtT + j], (double)val[0]);
+        // owner lanes hold distinct R slots: plain read-modify-write
+        if ((lane & (32 / RC - 1)) == 0 && lo < nR) wacc[warp][lo * kWrtT + j] += (float)val[0];
       }
+    }
+    __syncthreads();
+    // fold the warps' plane sums into the block totals in a fixed order
+    for (int k = threadIdx.x; k < NS; k += NTH) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < NTH / 32; ++w) {
+        t += (double)wacc[w][k];
+        wacc[w][k] = 0.f;
+      }
+      acc[k] += t;
     }
   }
   __syncthreads();
   const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-  for (int i = threadIdx.x; i < RC * kWrtT; i += NTH) partials[bid * (RC * kWrtT) + i] = acc[i];
+  for (int i = threadIdx.x; i < NS; i += NTH) partials[bid * NS + i] = acc[i];
 }
 
 // out[(R-1) tmax + (T-1)] from k_wilson_rt's per-block sums: one block per
@@ -1266,10 +1306,10 @@ cudaError_t launch_ape(const LatticeView& src, void* dst, double alpha, cudaStre
   SU2_DISPATCH(src.prec, {
     auto S = links_of<P>(src.links, src.g.vh);
     auto D = links_of<P>(dst, src.g.vh);
-    // three y-slices (one per spatial direction) share the machine
-    int gx = grid_for(k_ape<P>, 2 * src.g.vh) / 3;
+    // two y-slices (one per parity) share the machine
+    int gx = grid_for(k_ape<P>, 2 * src.g.vh) / 2;
     if (gx < 1) gx = 1;
-    k_ape<P><<<dim3(gx, 3), kThreads, 0, st>>>(S, D, src.g, alpha);
+    k_ape<P><<<dim3(gx, 2), kThreads, 0, st>>>(S, D, src.g, alpha);
   });
   count_launches(1);
   return cudaGetLastError();
@@ -1340,6 +1380,9 @@ static cudaError_t launch_wilson_plane(const LatticeView& v, const void* spatial
 #define SU2_WILSON_RT 1
 #endif
 constexpr int kWilsonRtThreads = 512;
+// dynamic shared memory of the time-outer kernel: 227 KB per block minus its
+// static accumulators (18 KB at RC = 16)
+constexpr int kWilsonRtSmemMax = 208 * 1024;
 
 template <int P, int RC>
 static cudaError_t launch_wilson_rt_rc(const LatticeView& v, const void* spatial, int rmax, int tmax, int smem,
@@ -1350,7 +1393,7 @@ static cudaError_t launch_wilson_rt_rc(const LatticeView& v, const void* spatial
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     cudaError_t e = cudaFuncSetAttribute(k_wilson_rt<P, RC, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kWilsonPlaneSmemMax);
+                                         kWilsonRtSmemMax);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
@@ -1367,7 +1410,8 @@ static cudaError_t launch_wilson_rt_rc(const LatticeView& v, const void* spatial
   if (gx < 1) gx = 1;
   auto Lt = links_of<P>(v.links, v.g.vh);
   auto Ls = links_of<P>(const_cast<void*>(spatial), v.g.vh);
-  k_wilson_rt<P, RC, NTH><<<dim3((unsigned)gx, nchunks), NTH, smem, st>>>(Ls, Lt, v.g, rmax, tmax, ntc, s.partials);
+  k_wilson_rt<P, RC, NTH><<<dim3((unsigned)gx, nchunks), NTH, smem, st>>>(Ls, Lt, v.g, rmax, tmax, ntc, nrc * RC,
+                                                                         s.partials);
   count_launches(1);
   const int64_t V = 2 * v.g.vh;
   k_wilson_rt_final<RC><<<rmax * tmax, kThreads, 0, st>>>(s.partials, (int)gx, ntc, tmax, 1.0 / (3.0 * (double)V),
@@ -1389,10 +1433,12 @@ static cudaError_t launch_wilson_rt(const LatticeView& v, const void* spatial, i
   if (!SU2_WILSON_RT) return cudaSuccess;
   const int nmax = v.g.n[0] > v.g.n[1] ? (v.g.n[0] > v.g.n[2] ? v.g.n[0] : v.g.n[2])
                                        : (v.g.n[1] > v.g.n[2] ? v.g.n[1] : v.g.n[2]);
-  const int smem = 2 * nmax * v.g.n[3] * (int)sizeof(Quat<R>);
-  if (smem > kWilsonPlaneSmemMax) return cudaSuccess;
+  const int rc = rmax <= 8 ? 8 : 16;
+  const int pad = (rmax + rc - 1) / rc * rc;  // columns a .. a + pad - 1 of a row
+  const int smem = 2 * (nmax + pad) * v.g.n[3] * (int)sizeof(Quat<R>);
+  if (smem > kWilsonRtSmemMax) return cudaSuccess;
   *used = true;
-  if (rmax <= 8) return launch_wilson_rt_rc<P, 8>(v, spatial, rmax, tmax, smem, s, st);
+  if (rc == 8) return launch_wilson_rt_rc<P, 8>(v, spatial, rmax, tmax, smem, s, st);
   return launch_wilson_rt_rc<P, 16>(v, spatial, rmax, tmax, smem, s, st);
   }
 }
