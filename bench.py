@@ -181,7 +181,8 @@ def source_sha():
     """Hash of the heat-bath kernel's sources and build flags."""
     h = hashlib.sha256()
     pkg = os.path.join(ROOT, "paper_1010_4834_gb300")
-    for f in (os.path.join(pkg, "csrc", "su2_device.cuh"), os.path.join(pkg, "csrc", "su2_kernels.cu"),
+    for f in (os.path.join(pkg, "csrc", "su2_device.cuh"), os.path.join(pkg, "csrc", "su2_heatbath.cu"),
+              os.path.join(pkg, "csrc", "su2_kernel_util.cuh"), os.path.join(pkg, "csrc", "su2_internal.h"),
               os.path.join(pkg, "build.py")):
         with open(f, "rb") as fh:
             h.update(fh.read())
@@ -337,6 +338,17 @@ def run_gpu_on_stream(args):
         extra["paper_mode"] = {"value": 20 * 4 * V / (a.elapsed_time(e) / 1e3), "unit": UNIT,
                                "what": "64^4 FP32, beta 6.0, hot start, Creutz sampler with one try, "
                                        "plaquette and Polyakov every sweep, 20 sweeps"}
+        # the layout comparison of Section 5.1 (same settings): one array of
+        # all links against one array per direction, one plain kernel on both
+        lat.layout_compare(1)
+        ms, mismatch = lat.layout_compare(8)
+        ups = [8 * 4 * V / (t / 1e3) for t in ms]
+        extra["layout"] = {"library": ups[0], "plain_by_direction": ups[1], "plain_one_array": ups[2],
+                           "unit": UNIT, "by_direction_over_one_array": ups[1] / ups[2],
+                           "mismatched_links": mismatch,
+                           "what": "8 sweeps in paper mode: the library's kernels; a plain one-thread-per-link "
+                                   "kernel on the library's layout (one array per direction and parity); the same "
+                                   "kernel on one site-major array (element 4 s + mu), the paper's layout"}
         lat.close()
         del lat
         for prec, n in (("f64", 4), ("f16q", 20)):

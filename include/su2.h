@@ -150,9 +150,29 @@ int su2_restart(su2_lattice* h, int start);
  * receives, for sweep i of this call, the three plaquette means (k = 0..2)
  * and the Polyakov loop (k = 3).  Results stay on the device until the end
  * of the call (one synchronisation per 1024 sweeps).  Advances the sweep
- * counter by n.
+ * counter by n.  The plaquette is summed inside the sweep (in the
+ * odd-parity substeps of mu = 1, 2, 3, from their staples), so it equals
+ * su2_plaquette of the new configuration up to the order of summation; the
+ * links are the same as after su2_heatbath_sweep.
  */
 int su2_sweep_measure(su2_lattice* h, int n, double* hist);
+
+/*
+ * The link-layout comparison of Section 5.1 (one array holding all links,
+ * the four directions of a site next to each other, against one array per
+ * direction), run on this GPU.  FP32 handles only (SU2_EINVAL otherwise);
+ * sweeps >= 1.  From the current configuration the call runs `sweeps`
+ * heat-bath sweeps three times: with the library's own kernels (ms[0]), with
+ * a plain one-thread-per-link kernel on the library's layout (ms[1]), and
+ * with the same plain kernel on a site-major single array, element
+ * 4 s + mu (ms[2]); ms[] are CUDA-event times on the handle's stream,
+ * conversions excluded.  *mismatch receives the number of 16-byte links in
+ * which the second and third results differ from the first (0 expected: the
+ * three run the same arithmetic).  The handle ends in the state of the first
+ * run (sweep counter advanced by `sweeps`).  Allocates and frees two link
+ * stores of device memory; synchronises.
+ */
+int su2_layout_compare(su2_lattice* h, int sweeps, double ms[3], uint64_t* mismatch);
 
 /*
  * One checkerboard substep (direction mu in 0..3, parity in 0..1) of the heat

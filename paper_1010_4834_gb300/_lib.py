@@ -49,6 +49,7 @@ SIGNATURES = {
     "su2_heatbath_substep": (_i, [_vp, _i, _i, _u32]),
     "su2_restart": (_i, [_vp, _i]),
     "su2_sweep_measure": (_i, [_vp, _i, _dp]),
+    "su2_layout_compare": (_i, [_vp, _i, _dp, C.POINTER(_u64)]),
     "su2_kernel_launches": (_i, [C.POINTER(_u64)]),
     "su2_overrelax_sweep": (_i, [_vp, _i]),
     "su2_plaquette": (_i, [_vp, _dp]),

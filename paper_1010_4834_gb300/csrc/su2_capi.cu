@@ -403,6 +403,77 @@ extern "C" int su2_sweep_measure(su2_lattice* h, int n, double* hist) {
   return SU2_OK;
 }
 
+extern "C" int su2_layout_compare(su2_lattice* h, int sweeps, double ms[3], uint64_t* mismatch) {
+  clear_error();
+  if (!h || !ms || !mismatch) return fail(SU2_EINVAL, "handle, ms and mismatch must not be NULL");
+  if (h->prec != SU2_F32) return fail(SU2_EINVAL, "the layout comparison runs on FP32 handles only");
+  if (sweeps < 1) return fail(SU2_EINVAL, "sweeps must be >= 1");
+  if (h->sweep + (uint64_t)sweeps >= 0xFFFFFFFFull) return fail(SU2_EINVAL, "sweep counter would reach the reserved index 2^32 - 1");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = h->stream;
+  const LatticeView v = view(h);
+  const HBParams hp = hb_params(h);
+  const size_t bytes = (size_t)8 * h->g.vh * 16;
+  void *start = nullptr, *first = nullptr, *other = nullptr;
+  unsigned long long* d_count = nullptr;
+  cudaEvent_t ev[6] = {};
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    if (start) cudaFree(start);
+    if (first) cudaFree(first);
+    if (other) cudaFree(other);
+    if (d_count) cudaFree(d_count);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  SU2_CU_CLEAN(cudaMalloc(&start, bytes), cleanup());
+  SU2_CU_CLEAN(cudaMalloc(&first, bytes), cleanup());
+  SU2_CU_CLEAN(cudaMalloc(&other, bytes), cleanup());
+  SU2_CU_CLEAN(cudaMalloc(&d_count, sizeof(unsigned long long)), cleanup());
+  for (auto& e : ev) SU2_CU_CLEAN(cudaEventCreate(&e), cleanup());
+  SU2_CU_CLEAN(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st), cleanup());
+  SU2_CU_CLEAN(cudaMemcpyAsync(start, h->links, bytes, cudaMemcpyDeviceToDevice, st), cleanup());
+  // 1. the library's kernels
+  SU2_CU_CLEAN(cudaEventRecord(ev[0], st), cleanup());
+  for (int i = 0; i < sweeps; ++i) SU2_CU_CLEAN(enqueue_sweep(h, (uint32_t)i, st), cleanup());
+  SU2_CU_CLEAN(cudaEventRecord(ev[1], st), cleanup());
+  SU2_CU_CLEAN(cudaMemcpyAsync(first, h->links, bytes, cudaMemcpyDeviceToDevice, st), cleanup());
+  // 2. the plain kernel on the library's layout
+  SU2_CU_CLEAN(cudaMemcpyAsync(h->links, start, bytes, cudaMemcpyDeviceToDevice, st), cleanup());
+  SU2_CU_CLEAN(cudaEventRecord(ev[2], st), cleanup());
+  for (int i = 0; i < sweeps; ++i)
+    for (int mu = 0; mu < 4; ++mu)
+      for (int p = 0; p < 2; ++p)
+        SU2_CU_CLEAN(launch_hb_plain(v, h->links, false, mu, p, h->d_sweep, (uint32_t)i, hp, st), cleanup());
+  SU2_CU_CLEAN(cudaEventRecord(ev[3], st), cleanup());
+  SU2_CU_CLEAN(launch_count_diff(h->links, first, bytes, d_count, st), cleanup());
+  // 3. the plain kernel on the site-major single array
+  SU2_CU_CLEAN(cudaMemcpyAsync(h->links, start, bytes, cudaMemcpyDeviceToDevice, st), cleanup());
+  SU2_CU_CLEAN(launch_site_major(v, other, true, st), cleanup());
+  SU2_CU_CLEAN(cudaEventRecord(ev[4], st), cleanup());
+  for (int i = 0; i < sweeps; ++i)
+    for (int mu = 0; mu < 4; ++mu)
+      for (int p = 0; p < 2; ++p)
+        SU2_CU_CLEAN(launch_hb_plain(v, other, true, mu, p, h->d_sweep, (uint32_t)i, hp, st), cleanup());
+  SU2_CU_CLEAN(cudaEventRecord(ev[5], st), cleanup());
+  SU2_CU_CLEAN(launch_site_major(v, other, false, st), cleanup());
+  SU2_CU_CLEAN(launch_count_diff(h->links, first, bytes, d_count, st), cleanup());
+  // the handle keeps the first run's result
+  SU2_CU_CLEAN(cudaMemcpyAsync(h->links, first, bytes, cudaMemcpyDeviceToDevice, st), cleanup());
+  SU2_CU_CLEAN(launch_add_u32(h->d_sweep, (uint32_t)sweeps, st), cleanup());
+  unsigned long long count = 0;
+  SU2_CU_CLEAN(cudaMemcpyAsync(&count, d_count, sizeof count, cudaMemcpyDeviceToHost, st), cleanup());
+  SU2_CU_CLEAN(cudaStreamSynchronize(st), cleanup());
+  float t[3];
+  for (int k = 0; k < 3; ++k) SU2_CU_CLEAN(cudaEventElapsedTime(&t[k], ev[2 * k], ev[2 * k + 1]), cleanup());
+  cleanup();
+  for (int k = 0; k < 3; ++k) ms[k] = t[k];
+  *mismatch = count;
+  h->sweep += (uint64_t)sweeps;
+  h->smeared = 0;
+  return SU2_OK;
+}
+
 extern "C" int su2_kernel_launches(uint64_t* n) {
   clear_error();
   if (!n) return fail(SU2_EINVAL, "n is NULL");

@@ -1,0 +1,247 @@
+// The checkerboard heat-bath substep for sm_103a (Section 2 Eqs. 5-9, 11;
+// Section 4), with its optional plaquette sum for measured sweeps, and the
+// kernel that turns those sums into the plaquette.  Paper: Cardoso & Bicudo,
+// arXiv:1010.4834.
+#include "su2_internal.h"
+#include "su2_kernel_util.cuh"
+
+namespace su2 {
+
+// ---------------------------------------------------------------------------
+// Heat-bath substep (Section 2 Eqs. 5-9, 11; Section 4 checkerboard): one
+// thread per link of direction MU on the parity-p sublattice.
+//
+// Most links accept their first a0 trial, but a warp would repeat the trial
+// loop until its slowest lane accepts.  So every lane makes trial 1 inline;
+// a link that rejects it goes to a block-wide shared-memory queue (its
+// W = Sigma/k, alpha, index and site), which the whole block drains every
+// kDeferEvery iterations with trials 2, 3, ...  The draws and their order are
+// those of the plain loop, so results are identical; only the schedule
+// differs.  A full queue falls back to finishing the link inline.
+//
+// With MEAS (the odd-parity substeps of MU = 1, 2, 3 of a measured sweep) the
+// kernel also adds up Tr(U_MU(x) L(x)^dagger)/2 over its links, with L the
+// staple's partial sum over NU < MU and U the link's final value (the
+// accepted draw as stored, or the kept old link), and writes one sum per
+// block to `meas`.  Every plaquette of a plane (NU, MU), NU < MU, holds two
+// MU-links on sites of opposite parity, so the odd-parity substep of MU counts
+// each of them once; and once that substep has run, every link in directions
+// <= MU has its end-of-sweep value.  The three substeps together give the
+// plaquette of Eq. 12 after the sweep (planes (0,1), (0,2) and (1,2) the
+// spatial part, (NU,3) the space-time part) without another pass over the
+// links.
+// ---------------------------------------------------------------------------
+constexpr int kDeferCap = 512;
+constexpr int kDeferEvery = 8;
+
+template <class R, bool MEAS> struct Deferred {
+  Quat<R> w;
+  R alpha;
+  int h;
+  uint32_t site;
+};
+template <class R> struct Deferred<R, true> {
+  Quat<R> w;
+  R alpha;
+  int h;
+  uint32_t site;
+  Quat<R> lower;
+};
+
+template <class R, bool MEAS>
+__device__ __forceinline__ int finish_deferred(const Deferred<R, MEAS>& d, uint4 ctr, const HBParams& hp,
+                                               Quat<R>* out) {
+  R a0;
+  const int n = sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0);
+  if (n) *out = compose_link<R>(a0, d.w, ctr, hp);
+  return n;
+}
+
+template <int P, int MU, bool MEAS>
+__global__ void __launch_bounds__(kThreads, Occ<P>::hb)
+    k_heatbath(Links<P> L, Geom g, int p, const uint32_t* sweep_base, uint32_t sweep_off,
+               const __grid_constant__ HBParams hp, unsigned long long* stats, double* meas) {
+  using R = typename Real<P>::T;
+  using M = Math<R>;
+  using Def = Deferred<R, MEAS>;
+  __shared__ Def queue[kDeferCap];
+  __shared__ int qn;
+  const R beta = (R)hp.beta;
+  const uint32_t sweep = (sweep_base ? *sweep_base : 0u) + sweep_off;
+  const uint32_t tag = (uint32_t)MU | hp.lattice_tag;
+  unsigned int trials = 0, capped = 0, haar = 0;
+  Acc<R> plaq;  // MEAS: plaquettes of the planes (NU < MU, MU)
+  if (threadIdx.x == 0) qn = 0;
+  __syncthreads();
+  const int vh = (int)g.vh;
+  const int stride = gridDim.x * blockDim.x;
+  int it = 0;
+  for (int base = blockIdx.x * blockDim.x; base < vh; base += stride, ++it) {
+    const int h = base + threadIdx.x;
+    if (h < vh) {
+      const Site x = site_from_half(g, (uint32_t)h, p);
+      Quat<R> lower;
+      Quat<R> sig;
+      if constexpr (MEAS) sig = staple_split<P, MU, true>(L, g, x, h, p, lower);
+      else sig = staple<P, MU, 0xF, true>(L, g, x, h, p);
+      const uint32_t site = site_index(g, x);
+      const uint4 ctr = make_uint4(site, tag, sweep, 0u);
+      const R k2 = qdot(sig, sig);
+      const R invk = M::rsqrt(k2);
+      const R alpha = beta * k2 * invk;
+      if (!(alpha >= R(1e-12))) {
+        uint4 c = ctr;
+        c.w = 1u;
+        const Quat<R> nl = haar_from<R>(philox(c, hp.rk));
+        if constexpr (MEAS) plaq.add(qdot(L.put(2 * MU + p, h, nl), lower));
+        else L.st(2 * MU + p, h, nl);
+        haar += 1;
+      } else {
+        const R inv2a = trial_inv2a(alpha);
+        const R e = trial_e(alpha, hp.sampler);
+        const Quat<R> w = qscale(sig, invk);
+        R a0;
+        if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0)) {
+          const Quat<R> nl = compose_link<R>(a0, w, ctr, hp);
+          if constexpr (MEAS) plaq.add(qdot(L.put(2 * MU + p, h, nl), lower));
+          else L.st(2 * MU + p, h, nl);
+          trials += 1;
+        } else if (hp.max_tries > 1) {
+          const int slot = atomicAdd(&qn, 1);
+          Def d;
+          d.w = w;
+          d.alpha = alpha;
+          d.h = h;
+          d.site = site;
+          if constexpr (MEAS) d.lower = lower;
+          if (slot < kDeferCap) {
+            queue[slot] = d;
+          } else {
+            Quat<R> nl;
+            const int n = finish_deferred<R, MEAS>(d, ctr, hp, &nl);
+            if constexpr (MEAS) plaq.add(qdot(n ? L.put(2 * MU + p, h, nl) : L.ld(2 * MU + p, h), lower));
+            else if (n) L.st(2 * MU + p, h, nl);
+            trials += n ? (unsigned)n : (unsigned)hp.max_tries;
+            capped += n == 0;
+          }
+        } else {
+          if constexpr (MEAS) plaq.add(qdot(L.ld(2 * MU + p, h), lower));
+          trials += 1;
+          capped += 1;
+        }
+      }
+    }
+    if ((it % kDeferEvery) == kDeferEvery - 1 || base + stride >= vh) {
+      __syncthreads();
+      const int n = min(qn, kDeferCap);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Def d = queue[i];
+        Quat<R> nl;
+        const int t = finish_deferred<R, MEAS>(d, make_uint4(d.site, tag, sweep, 0u), hp, &nl);
+        if constexpr (MEAS) plaq.add(qdot(t ? L.put(2 * MU + p, d.h, nl) : L.ld(2 * MU + p, d.h), d.lower));
+        else if (t) L.st(2 * MU + p, d.h, nl);
+        trials += t ? (unsigned)t : (unsigned)hp.max_tries;
+        capped += t == 0;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) qn = 0;
+      __syncthreads();
+    }
+  }
+  if (MEAS) {
+    __shared__ double shp[kThreads / 32];
+    const double v = warp_sum(plaq.value());
+    if ((threadIdx.x & 31) == 0) shp[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) t += shp[w];
+      meas[blockIdx.x] = t;
+    }
+  }
+  if (stats) {
+    __shared__ unsigned int sh[3];
+    if (threadIdx.x < 3) sh[threadIdx.x] = 0;
+    __syncthreads();
+    if (trials) atomicAdd(&sh[0], trials);
+    if (capped) atomicAdd(&sh[1], capped);
+    if (haar) atomicAdd(&sh[2], haar);
+    __syncthreads();
+    if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(stats + threadIdx.x, (unsigned long long)sh[threadIdx.x]);
+  }
+}
+
+// The plaquette after a measured sweep from the block sums of its three MEAS
+// substeps: meas[k * stride + b], k = 0, 1, 2 for MU = 1, 2, 3, b < nb[k].
+// One block; fixed-order compensated sums.  out = {all, spatial, space-time}
+// means of Tr/2 (Eq. 13).
+__global__ void __launch_bounds__(kThreads) k_plaquette_from_sweep(const double* meas, int stride, int nb1, int nb2,
+                                                                   int nb3, double volume, double* out) {
+  __shared__ double ss[kThreads / 32][3], sc[kThreads / 32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nb[3] = {nb1, nb2, nb3};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    KSum a;
+    for (int b = threadIdx.x; b < nb[k]; b += kThreads) a.add(meas[(size_t)k * stride + b]);
+    a = warp_ksum(a);
+    if (lane == 0) {
+      ss[warp][k] = a.s;
+      sc[warp][k] = a.c;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      KSum a;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        KSum o;
+        o.s = ss[w][k];
+        o.c = sc[w][k];
+        a = ksum_combine(a, o);
+      }
+      tot[k] = a.value();
+    }
+    const double S = tot[0] + tot[1], T = tot[2];
+    const double n3 = 3.0 * volume;
+    out[0] = (S + T) / (2.0 * n3);
+    out[1] = S / n3;
+    out[2] = T / n3;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint32_t* sweep_base,
+                            uint32_t sweep_off, const HBParams& hp, unsigned long long* stats,
+                            cudaStream_t st, double* meas, int* meas_blocks) {
+  if (meas && (mu < 1 || parity != 1 || !meas_blocks)) return cudaErrorInvalidValue;
+  SU2_DISPATCH(v.prec, SU2_DISPATCH_MU(mu, {
+    auto L = links_of<P>(v.links, v.g.vh);
+    if (meas) {
+      if constexpr (MU >= 1) {
+        const int gr = grid_for(k_heatbath<P, MU, true>, v.g.vh);
+        if (gr > kMeasStride) return cudaErrorInvalidConfiguration;
+        *meas_blocks = gr;
+        k_heatbath<P, MU, true><<<gr, kThreads, 0, st>>>(L, v.g, parity, sweep_base, sweep_off, hp, stats, meas);
+      }
+    } else {
+      const int gr = grid_for(k_heatbath<P, MU, false>, v.g.vh);
+      k_heatbath<P, MU, false><<<gr, kThreads, 0, st>>>(L, v.g, parity, sweep_base, sweep_off, hp, stats, nullptr);
+    }
+  }));
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plaquette_from_sweep(const double* meas, const int nb[3], int64_t volume, double* out,
+                                        cudaStream_t st) {
+  k_plaquette_from_sweep<<<1, kThreads, 0, st>>>(meas, kMeasStride, nb[0], nb[1], nb[2], (double)volume, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace su2

@@ -67,6 +67,15 @@ cudaError_t launch_to_canonical(const LatticeView& v, double* canon, int64_t s0,
 cudaError_t launch_from_canonical(const LatticeView& v, const double* canon, int64_t s0,
                                   int64_t ns, cudaStream_t st);
 cudaError_t launch_add_u32(uint32_t* p, uint32_t v, cudaStream_t st);
+// Layout comparison (FP32): the plain heat-bath substep on the store `links`
+// in the library's layout or in the site-major single-array layout, the
+// conversion between v.links and a site-major copy, and a count of differing
+// 16-byte words of two buffers (added to *count).
+cudaError_t launch_hb_plain(const LatticeView& v, void* links, bool site_major, int mu, int parity,
+                            const uint32_t* sweep_base, uint32_t sweep_off, const HBParams& hp, cudaStream_t st);
+cudaError_t launch_site_major(const LatticeView& v, void* site_major, bool to_site_major, cudaStream_t st);
+cudaError_t launch_count_diff(const void* a, const void* b, size_t bytes, unsigned long long* count,
+                              cudaStream_t st);
 
 // Process-wide count of kernels this library launched (graph replays add
 // their kernel-node count through count_launches).

@@ -1,7 +1,7 @@
-// Kernels of the SU(2) heat-bath Monte Carlo for sm_103a: start
-// configurations, the checkerboard heat-bath and over-relaxation substeps,
-// the fused plaquette / Polyakov reductions, APE smearing, Wilson loops and
-// the canonical-layout conversions.  Paper: Cardoso & Bicudo,
+// Kernels of the SU(2) heat-bath Monte Carlo for sm_103a, except the
+// heat-bath substep itself (su2_heatbath.cu): start configurations, the
+// over-relaxation substep, the fused plaquette / Polyakov reductions, APE
+// smearing, Wilson loops and the canonical-layout conversions.  Paper: Cardoso & Bicudo,
 // arXiv:1010.4834 (Sections 2 and 4).
 //
 // None of this work is a dense contraction (2x2 SU(2) products in
@@ -14,10 +14,9 @@
 #include <cfloat>
 
 #include "su2_internal.h"
+#include "su2_kernel_util.cuh"
 
 namespace su2 {
-
-constexpr int kThreads = 256;
 
 static std::atomic<uint64_t> g_launches{0};
 static thread_local int g_capturing = 0;
@@ -67,150 +66,6 @@ size_t scratch_bytes() {
   return kScratchPartials * sizeof(double) + 256 + kScratchOut * sizeof(double) + 256;
 }
 
-// Blocks for `work` items with a grid-stride loop: every SM filled to the
-// kernel's occupancy, never more blocks than items need.
-template <class K>
-static int grid_for(K kernel, int64_t work, int smem = 0) {
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
-  if (per_sm < 1) per_sm = 1;
-  const int64_t full = (int64_t)device_info().sms * per_sm;
-  const int64_t need = (work + kThreads - 1) / kThreads;
-  int64_t g = need < full ? need : full;
-  return (int)(g < 1 ? 1 : g);
-}
-
-// ---------------------------------------------------------------------------
-// Reduction helpers
-// ---------------------------------------------------------------------------
-template <class R> struct Acc;  // per-thread accumulator
-
-// FP32: Neumaier-compensated, so a thread's many small terms keep FP32
-// rounding from growing with the count.
-template <> struct Acc<float> {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float t = s + v;
-    c += fabsf(s) >= fabsf(v) ? (s - t) + v : (v - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-
-template <> struct Acc<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double v) { s += v; }
-  __device__ __forceinline__ double value() const { return s; }
-};
-
-struct KSum {
-  double s = 0.0, c = 0.0;
-  __device__ __forceinline__ void add(double v) {
-    const double t = s + v;
-    c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return s + c; }
-};
-
-template <class T> __device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block-sum NV doubles into partials[block*NV + k]; returns true in the last
-// block to finish (all partials then visible to it).
-template <int NV>
-__device__ __forceinline__ bool block_partial(double (&v)[NV], double* partials,
-                                              unsigned int* counter) {
-  __shared__ double sh[kThreads / 32][NV];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
-  }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double t = lane < kThreads / 32 ? sh[lane][k] : 0.0;
-      t = warp_sum(t);
-      if (lane == 0) partials[(size_t)blockIdx.x * NV + k] = t;
-    }
-    if (lane == 0) {
-      __threadfence();
-      const unsigned int ticket = atomicAdd(counter, 1u);
-      last = (ticket == gridDim.x - 1);
-    }
-  }
-  __syncthreads();
-  return last;
-}
-
-// Neumaier pairs combine as (a.s + b.s with its rounding error) + a.c + b.c.
-__device__ __forceinline__ KSum ksum_combine(KSum a, const KSum& b) {
-  a.add(b.s);
-  a.c += b.c;
-  return a;
-}
-
-// Fixed-order tree over the lanes of a warp; lane 0 ends with the total.
-__device__ __forceinline__ KSum warp_ksum(KSum a) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    KSum o;
-    o.s = __shfl_xor_sync(0xffffffffu, a.s, off);
-    o.c = __shfl_xor_sync(0xffffffffu, a.c, off);
-    a = ksum_combine(a, o);
-  }
-  return a;
-}
-
-// In the last block: tot[k] = sum over blocks of partials[b*NV + k].  Every
-// thread adds a strided subset (compensated), then a fixed-order tree over
-// lanes and warps combines them, so the result does not depend on timing and
-// no thread runs a long serial FP64 chain.
-template <int NV>
-__device__ __forceinline__ void final_sum(const double* partials, int nblocks, double (&tot)[NV]) {
-  __shared__ double ss[kThreads / 32][NV], sc[kThreads / 32][NV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    KSum a;
-    for (int b = threadIdx.x; b < nblocks; b += kThreads) a.add(__ldcg(partials + (size_t)b * NV + k));
-    a = warp_ksum(a);
-    if (lane == 0) {
-      ss[warp][k] = a.s;
-      sc[warp][k] = a.c;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      KSum a;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        KSum o;
-        o.s = ss[w][k];
-        o.c = sc[w][k];
-        a = ksum_combine(a, o);
-      }
-      tot[k] = a.value();
-    }
-  }
-}
-
-// Occupancy targets (blocks of 256 per SM) for the register-heavy kernels.
-#ifndef SU2_HB_MINB
-#define SU2_HB_MINB 4
-#endif
-template <int P> struct Occ { static constexpr int hb = SU2_HB_MINB; };
-template <> struct Occ<kF64> { static constexpr int hb = 2; };
-
 // ---------------------------------------------------------------------------
 // Start configurations (Section 4 kernel list: cold start U = 1, hot start a
 // random SU(2) matrix, read here as Haar via Philox draw 0 of sweep index
@@ -230,211 +85,6 @@ __global__ void __launch_bounds__(kThreads) k_init(Links<P> L, Geom g, int start
     Quat<R> q = qone<R>();
     if (start) q = haar_from<R>(philox(make_uint4(s, (uint32_t)mu | lattice_tag, 0xFFFFFFFFu, 0u), rk));
     L.st(2 * mu + parity(x), hidx(g, x), q);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Heat-bath substep (Section 2 Eqs. 5-9, 11; Section 4 checkerboard): one
-// thread per link of direction MU on the parity-p sublattice.
-//
-// Most links accept their first a0 trial, but a warp would repeat the trial
-// loop until its slowest lane accepts.  So every lane makes trial 1 inline;
-// a link that rejects it goes to a block-wide shared-memory queue (its
-// W = Sigma/k, alpha, index and site), which the whole block drains every
-// kDeferEvery iterations with trials 2, 3, ...  The draws and their order are
-// those of the plain loop, so results are identical; only the schedule
-// differs.  A full queue falls back to finishing the link inline.
-//
-// With MEAS (the odd-parity substeps of MU = 1, 2, 3 of a measured sweep) the
-// kernel also adds up Tr(U_MU(x) L(x)^dagger)/2 over its links, with L the
-// staple's partial sum over NU < MU and U the link's final value (the
-// accepted draw as stored, or the kept old link), and writes one sum per
-// block to `meas`.  Every plaquette of a plane (NU, MU), NU < MU, holds two
-// MU-links on sites of opposite parity, so the odd-parity substep of MU counts
-// each of them once; and once that substep has run, every link in directions
-// <= MU has its end-of-sweep value.  The three substeps together give the
-// plaquette of Eq. 12 after the sweep (planes (0,1), (0,2) and (1,2) the
-// spatial part, (NU,3) the space-time part) without another pass over the
-// links.
-// ---------------------------------------------------------------------------
-constexpr int kDeferCap = 512;
-constexpr int kDeferEvery = 8;
-
-template <class R, bool MEAS> struct Deferred {
-  Quat<R> w;
-  R alpha;
-  int h;
-  uint32_t site;
-};
-template <class R> struct Deferred<R, true> {
-  Quat<R> w;
-  R alpha;
-  int h;
-  uint32_t site;
-  Quat<R> lower;
-};
-
-template <class R, bool MEAS>
-__device__ __forceinline__ int finish_deferred(const Deferred<R, MEAS>& d, uint4 ctr, const HBParams& hp,
-                                               Quat<R>* out) {
-  R a0;
-  const int n = sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0);
-  if (n) *out = compose_link<R>(a0, d.w, ctr, hp);
-  return n;
-}
-
-template <int P, int MU, bool MEAS>
-__global__ void __launch_bounds__(kThreads, Occ<P>::hb)
-    k_heatbath(Links<P> L, Geom g, int p, const uint32_t* sweep_base, uint32_t sweep_off,
-               const __grid_constant__ HBParams hp, unsigned long long* stats, double* meas) {
-  using R = typename Real<P>::T;
-  using M = Math<R>;
-  using Def = Deferred<R, MEAS>;
-  __shared__ Def queue[kDeferCap];
-  __shared__ int qn;
-  const R beta = (R)hp.beta;
-  const uint32_t sweep = (sweep_base ? *sweep_base : 0u) + sweep_off;
-  const uint32_t tag = (uint32_t)MU | hp.lattice_tag;
-  unsigned int trials = 0, capped = 0, haar = 0;
-  Acc<R> plaq;  // MEAS: plaquettes of the planes (NU < MU, MU)
-  if (threadIdx.x == 0) qn = 0;
-  __syncthreads();
-  const int vh = (int)g.vh;
-  const int stride = gridDim.x * blockDim.x;
-  int it = 0;
-  for (int base = blockIdx.x * blockDim.x; base < vh; base += stride, ++it) {
-    const int h = base + threadIdx.x;
-    if (h < vh) {
-      const Site x = site_from_half(g, (uint32_t)h, p);
-      Quat<R> lower;
-      Quat<R> sig;
-      if constexpr (MEAS) sig = staple_split<P, MU, true>(L, g, x, h, p, lower);
-      else sig = staple<P, MU, 0xF, true>(L, g, x, h, p);
-      const uint32_t site = site_index(g, x);
-      const uint4 ctr = make_uint4(site, tag, sweep, 0u);
-      const R k2 = qdot(sig, sig);
-      const R invk = M::rsqrt(k2);
-      const R alpha = beta * k2 * invk;
-      if (!(alpha >= R(1e-12))) {
-        uint4 c = ctr;
-        c.w = 1u;
-        const Quat<R> nl = haar_from<R>(philox(c, hp.rk));
-        if constexpr (MEAS) plaq.add(qdot(L.put(2 * MU + p, h, nl), lower));
-        else L.st(2 * MU + p, h, nl);
-        haar += 1;
-      } else {
-        const R inv2a = trial_inv2a(alpha);
-        const R e = trial_e(alpha, hp.sampler);
-        const Quat<R> w = qscale(sig, invk);
-        R a0;
-        if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0)) {
-          const Quat<R> nl = compose_link<R>(a0, w, ctr, hp);
-          if constexpr (MEAS) plaq.add(qdot(L.put(2 * MU + p, h, nl), lower));
-          else L.st(2 * MU + p, h, nl);
-          trials += 1;
-        } else if (hp.max_tries > 1) {
-          const int slot = atomicAdd(&qn, 1);
-          Def d;
-          d.w = w;
-          d.alpha = alpha;
-          d.h = h;
-          d.site = site;
-          if constexpr (MEAS) d.lower = lower;
-          if (slot < kDeferCap) {
-            queue[slot] = d;
-          } else {
-            Quat<R> nl;
-            const int n = finish_deferred<R, MEAS>(d, ctr, hp, &nl);
-            if constexpr (MEAS) plaq.add(qdot(n ? L.put(2 * MU + p, h, nl) : L.ld(2 * MU + p, h), lower));
-            else if (n) L.st(2 * MU + p, h, nl);
-            trials += n ? (unsigned)n : (unsigned)hp.max_tries;
-            capped += n == 0;
-          }
-        } else {
-          if constexpr (MEAS) plaq.add(qdot(L.ld(2 * MU + p, h), lower));
-          trials += 1;
-          capped += 1;
-        }
-      }
-    }
-    if ((it % kDeferEvery) == kDeferEvery - 1 || base + stride >= vh) {
-      __syncthreads();
-      const int n = min(qn, kDeferCap);
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const Def d = queue[i];
-        Quat<R> nl;
-        const int t = finish_deferred<R, MEAS>(d, make_uint4(d.site, tag, sweep, 0u), hp, &nl);
-        if constexpr (MEAS) plaq.add(qdot(t ? L.put(2 * MU + p, d.h, nl) : L.ld(2 * MU + p, d.h), d.lower));
-        else if (t) L.st(2 * MU + p, d.h, nl);
-        trials += t ? (unsigned)t : (unsigned)hp.max_tries;
-        capped += t == 0;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) qn = 0;
-      __syncthreads();
-    }
-  }
-  if (MEAS) {
-    __shared__ double shp[kThreads / 32];
-    const double v = warp_sum(plaq.value());
-    if ((threadIdx.x & 31) == 0) shp[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) t += shp[w];
-      meas[blockIdx.x] = t;
-    }
-  }
-  if (stats) {
-    __shared__ unsigned int sh[3];
-    if (threadIdx.x < 3) sh[threadIdx.x] = 0;
-    __syncthreads();
-    if (trials) atomicAdd(&sh[0], trials);
-    if (capped) atomicAdd(&sh[1], capped);
-    if (haar) atomicAdd(&sh[2], haar);
-    __syncthreads();
-    if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(stats + threadIdx.x, (unsigned long long)sh[threadIdx.x]);
-  }
-}
-
-// The plaquette after a measured sweep from the block sums of its three MEAS
-// substeps: meas[k * stride + b], k = 0, 1, 2 for MU = 1, 2, 3, b < nb[k].
-// One block; fixed-order compensated sums.  out = {all, spatial, space-time}
-// means of Tr/2 (Eq. 13).
-__global__ void __launch_bounds__(kThreads) k_plaquette_from_sweep(const double* meas, int stride, int nb1, int nb2,
-                                                                   int nb3, double volume, double* out) {
-  __shared__ double ss[kThreads / 32][3], sc[kThreads / 32][3];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nb[3] = {nb1, nb2, nb3};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    KSum a;
-    for (int b = threadIdx.x; b < nb[k]; b += kThreads) a.add(meas[(size_t)k * stride + b]);
-    a = warp_ksum(a);
-    if (lane == 0) {
-      ss[warp][k] = a.s;
-      sc[warp][k] = a.c;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      KSum a;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        KSum o;
-        o.s = ss[w][k];
-        o.c = sc[w][k];
-        a = ksum_combine(a, o);
-      }
-      tot[k] = a.value();
-    }
-    const double S = tot[0] + tot[1], T = tot[2];
-    const double n3 = 3.0 * volume;
-    out[0] = (S + T) / (2.0 * n3);
-    out[1] = S / n3;
-    out[2] = T / n3;
   }
 }
 
@@ -1206,30 +856,6 @@ __global__ void k_add_u32(uint32_t* p, uint32_t v) { *p += v; }
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
-template <int P> static Links<P> links_of(void* base, int64_t vh) {
-  Links<P> L;
-  L.p = reinterpret_cast<decltype(L.p)>(base);
-  L.vh = vh;
-  return L;
-}
-
-#define SU2_DISPATCH(prec, ...)                                  \
-  switch (prec) {                                                \
-    case kF64: { constexpr int P = kF64; __VA_ARGS__; break; }   \
-    case kF32: { constexpr int P = kF32; __VA_ARGS__; break; }   \
-    case kF16Q: { constexpr int P = kF16Q; __VA_ARGS__; break; } \
-    default: return cudaErrorInvalidValue;                       \
-  }
-
-#define SU2_DISPATCH_MU(mu, ...)                          \
-  switch (mu) {                                           \
-    case 0: { constexpr int MU = 0; __VA_ARGS__; break; } \
-    case 1: { constexpr int MU = 1; __VA_ARGS__; break; } \
-    case 2: { constexpr int MU = 2; __VA_ARGS__; break; } \
-    case 3: { constexpr int MU = 3; __VA_ARGS__; break; } \
-    default: return cudaErrorInvalidValue;                \
-  }
-
 cudaError_t launch_init(const LatticeView& v, int start, PhiloxKey key, uint32_t lattice_tag,
                         cudaStream_t st) {
   const RoundKeys rk = round_keys(key);
@@ -1238,35 +864,6 @@ cudaError_t launch_init(const LatticeView& v, int start, PhiloxKey key, uint32_t
     const int gr = grid_for(k_init<P>, 8 * v.g.vh);
     k_init<P><<<gr, kThreads, 0, st>>>(L, v.g, start, rk, lattice_tag);
   });
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint32_t* sweep_base,
-                            uint32_t sweep_off, const HBParams& hp, unsigned long long* stats,
-                            cudaStream_t st, double* meas, int* meas_blocks) {
-  if (meas && (mu < 1 || parity != 1 || !meas_blocks)) return cudaErrorInvalidValue;
-  SU2_DISPATCH(v.prec, SU2_DISPATCH_MU(mu, {
-    auto L = links_of<P>(v.links, v.g.vh);
-    if (meas) {
-      if constexpr (MU >= 1) {
-        const int gr = grid_for(k_heatbath<P, MU, true>, v.g.vh);
-        if (gr > kMeasStride) return cudaErrorInvalidConfiguration;
-        *meas_blocks = gr;
-        k_heatbath<P, MU, true><<<gr, kThreads, 0, st>>>(L, v.g, parity, sweep_base, sweep_off, hp, stats, meas);
-      }
-    } else {
-      const int gr = grid_for(k_heatbath<P, MU, false>, v.g.vh);
-      k_heatbath<P, MU, false><<<gr, kThreads, 0, st>>>(L, v.g, parity, sweep_base, sweep_off, hp, stats, nullptr);
-    }
-  }));
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_plaquette_from_sweep(const double* meas, const int nb[3], int64_t volume, double* out,
-                                        cudaStream_t st) {
-  k_plaquette_from_sweep<<<1, kThreads, 0, st>>>(meas, kMeasStride, nb[0], nb[1], nb[2], (double)volume, out);
   count_launches(1);
   return cudaGetLastError();
 }

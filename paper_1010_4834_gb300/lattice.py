@@ -113,6 +113,16 @@ class Lattice:
         check(_lib.load().su2_sweep_measure(self._h, int(n), _dptr(out)))
         return out
 
+    def layout_compare(self, sweeps):
+        """Section 5.1's layout comparison on this GPU (FP32): ms of `sweeps`
+        sweeps with the library's kernels, with a plain kernel on the
+        library's layout and on a site-major single array, and the number of
+        links in which the latter two results differ from the first."""
+        ms = np.empty(3)
+        n = C.c_uint64()
+        check(_lib.load().su2_layout_compare(self._h, int(sweeps), _dptr(ms), C.byref(n)))
+        return ms, n.value
+
     def substep(self, mu, parity, sweep_index):
         check(_lib.load().su2_heatbath_substep(self._h, int(mu), int(parity), int(sweep_index)))
 

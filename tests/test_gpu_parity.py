@@ -506,6 +506,30 @@ def test_sweep_plaquette_full_size_grid(beta):
     b.close()
 
 
+@pytest.mark.parametrize("dims,max_tries", [((8, 6, 4, 10), 64), ((16, 16, 16, 16), 64), ((8, 8, 8, 8), 1)])
+def test_layout_comparison_runs_the_same_chain(dims, max_tries):
+    # Section 5.1's one-array layout and the plain kernel on the library's
+    # layout leave the same links as the library's kernels; the handle keeps
+    # that result and the counter advances
+    a = Lattice(dims, 2.4, seed=9, start="hot", prec="f32")
+    b = Lattice(dims, 2.4, seed=9, start="hot", prec="f32")
+    for lat in (a, b):
+        lat.set_options(max_tries=max_tries)
+    ms, mismatch = a.layout_compare(3)
+    assert mismatch == 0
+    assert np.all(ms > 0)
+    b.sweep(3)
+    np.testing.assert_array_equal(a.get_links(), b.get_links())
+    assert a.sweep_count == 3
+    with pytest.raises(SU2Error):
+        a.layout_compare(0)
+    c = Lattice((4, 4, 4, 4), 2.0, prec="f64")
+    with pytest.raises(SU2Error):
+        c.layout_compare(1)
+    for lat in (a, b, c):
+        lat.close()
+
+
 def test_work_is_ordered_on_the_torch_stream():
     import torch
     s = torch.cuda.Stream()
