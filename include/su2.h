@@ -253,6 +253,13 @@ int su2_get_links(su2_lattice* h, double* host);
 int su2_set_links(su2_lattice* h, const double* host);
 
 /*
+ * The links of sites [first, first + count) (lexicographic site index, as in
+ * the canonical layout) into host[16 * count], for lattices too large to
+ * copy whole.  SU2_EINVAL if the range leaves the lattice.  Synchronises.
+ */
+int su2_get_sites(su2_lattice* h, int64_t first, int64_t count, double* host);
+
+/*
  * Number of CUDA kernels this library has launched in this process (all
  * handles; a replayed sweep graph counts each of its kernels).
  */

@@ -58,6 +58,7 @@ SIGNATURES = {
     "su2_ape_smear": (_i, [_vp, _d, _i]),
     "su2_wilson_loops": (_i, [_vp, _i, _i, _i, _dp]),
     "su2_get_links": (_i, [_vp, _dp]),
+    "su2_get_sites": (_i, [_vp, C.c_int64, C.c_int64, _dp]),
     "su2_set_links": (_i, [_vp, _dp]),
     "su2_sweep_count": (_i, [_vp, C.POINTER(_u64)]),
     "su2_set_sweep_count": (_i, [_vp, _u64]),

@@ -562,19 +562,33 @@ extern "C" int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smea
   return fetch_out(h, Rmax * Tmax, out);
 }
 
-extern "C" int su2_get_links(su2_lattice* h, double* host) {
-  clear_error();
-  if (!h || !host) return fail(SU2_EINVAL, "NULL argument");
+// Sites [first, first + count) in canonical FP64 order into host[16 * count].
+static int copy_sites_out(su2_lattice* h, int64_t first, int64_t count, double* host) {
   DeviceGuard dg(h->device);
-  const int64_t V = 2 * h->g.vh;
-  for (int64_t s0 = 0; s0 < V; s0 += h->staging_sites) {
-    const int64_t ns = V - s0 < h->staging_sites ? V - s0 : h->staging_sites;
-    SU2_CU(launch_to_canonical(view(h), h->staging, s0, ns, h->stream));
-    SU2_CU(cudaMemcpyAsync(host + 16 * s0, h->staging, (size_t)ns * 16 * sizeof(double),
+  for (int64_t k = 0; k < count; k += h->staging_sites) {
+    const int64_t ns = count - k < h->staging_sites ? count - k : h->staging_sites;
+    SU2_CU(launch_to_canonical(view(h), h->staging, first + k, ns, h->stream));
+    SU2_CU(cudaMemcpyAsync(host + 16 * k, h->staging, (size_t)ns * 16 * sizeof(double),
                            cudaMemcpyDeviceToHost, h->stream));
   }
   SU2_CU(cudaStreamSynchronize(h->stream));
   return SU2_OK;
+}
+
+extern "C" int su2_get_links(su2_lattice* h, double* host) {
+  clear_error();
+  if (!h || !host) return fail(SU2_EINVAL, "NULL argument");
+  return copy_sites_out(h, 0, 2 * h->g.vh, host);
+}
+
+extern "C" int su2_get_sites(su2_lattice* h, int64_t first, int64_t count, double* host) {
+  clear_error();
+  if (!h || (!host && count > 0)) return fail(SU2_EINVAL, "NULL argument");
+  const int64_t V = 2 * h->g.vh;
+  if (first < 0 || count < 0 || first > V || count > V - first)
+    return fail(SU2_EINVAL, "sites [%lld, %lld) outside the lattice of %lld sites", (long long)first,
+                (long long)(first + count), (long long)V);
+  return copy_sites_out(h, first, count, host);
 }
 
 extern "C" int su2_set_links(su2_lattice* h, const double* host) {

@@ -174,13 +174,13 @@ __global__ void __launch_bounds__(kThreads) k_plaquette(Links<P> L, Geom g, doub
                                                         unsigned int* counter, double* out) {
   using R = typename Real<P>::T;
   Acc<R> sp, tm;
-  const int V = (int)(2 * g.vh);
-  const int stride = gridDim.x * blockDim.x;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  for (; s < V; s += stride) {
+  const int64_t V = 2 * g.vh;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // 64-bit loop index: V may come within one stride of 2^31
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
     PlaqLinks<P> k0;
     int p0;
-    plaq_load<P>(L, g, s, k0, p0);
+    plaq_load<P>(L, g, (int)s, k0, p0);
     R ss0, ts0;
     plaq_sums<P>(k0, ss0, ts0);
     sp.add(ss0);
@@ -440,12 +440,12 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson(Links<P> Ls, Links<P>
   const int nT = min(TC, tmax - t0);
   for (int i = threadIdx.x; i < kWilsonMaxR * TC; i += blockDim.x) acc[i] = 0.0;
   __syncthreads();
-  const int V = (int)(2 * g.vh);
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < V; base += stride) {
-    const int s = base + threadIdx.x;
+  const int64_t V = 2 * g.vh;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < V; base += stride) {
+    const int64_t s = base + threadIdx.x;
     const bool valid = s < V;
-    const int sv = valid ? s : 0;
+    const int sv = valid ? (int)s : 0;
     if (mu == 0) wilson_site<P, TC, 0>(Ls, Lt, g, sv, valid, rmax, t0, nT, acc);
     else if (mu == 1) wilson_site<P, TC, 1>(Ls, Lt, g, sv, valid, rmax, t0, nT, acc);
     else wilson_site<P, TC, 2>(Ls, Lt, g, sv, valid, rmax, t0, nT, acc);

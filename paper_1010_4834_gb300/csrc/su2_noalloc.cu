@@ -95,11 +95,11 @@ __global__ void __launch_bounds__(kStaticThreads) k_plaquette_static(Links<P> L,
   __shared__ double fin[kStaticThreads][4];
   __shared__ bool last;
   SAcc<R> sp, tm;
-  const int V = (int)(2 * g.vh);
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < V; s += gridDim.x * blockDim.x) {
+  const int64_t V = 2 * g.vh;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < V; s += (int64_t)gridDim.x * blockDim.x) {
     const Site x = site_from_index(g, (uint32_t)s);
     const int p = parity(x), q = p ^ 1;
-    const int h = s >> 1;
+    const int h = (int)(s >> 1);
     const Quat<R> u0 = L.ld(0 + p, h), u1 = L.ld(2 + p, h), u2 = L.ld(4 + p, h), u3 = L.ld(6 + p, h);
     const int h0 = hidx(g, shifted<0, +1>(g, x));
     const int h1 = hidx(g, shifted<1, +1>(g, x));

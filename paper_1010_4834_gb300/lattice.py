@@ -37,6 +37,13 @@ def kernel_launches():
     return n.value
 
 
+def required_bytes(dims, prec):
+    """Device bytes a lattice of these extents and precision needs."""
+    n = C.c_size_t()
+    check(_lib.load().su2_required_bytes(dims_arg(tuple(int(d) for d in dims)), _lib.PREC[prec], C.byref(n)))
+    return n.value
+
+
 class Lattice:
     """One SU(2) lattice with links on the GPU (see include/su2.h).
 
@@ -165,6 +172,12 @@ class Lattice:
             out = np.empty((self.volume, 4, 4))
         assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.volume * 16
         check(_lib.load().su2_get_links(self._h, _dptr(out)))
+        return out
+
+    def get_sites(self, first, count):
+        """Canonical FP64 links of sites [first, first + count): shape (count, 4, 4)."""
+        out = np.empty((int(count), 4, 4))
+        check(_lib.load().su2_get_sites(self._h, int(first), int(count), _dptr(out)))
         return out
 
     def set_links(self, U):
