@@ -415,6 +415,8 @@ struct Geom {
   int64_t vh;       // V / 2
   int st[4];        // row stride of a unit step in direction 1..3 (st[0] unused)
   int wr[4];        // st[d] * (n[d] - 1): row change of a wrapping step
+  int hst[4];       // n0h * st[d]: half-index change of a unit step in direction d >= 1
+  int hwr[4];       // n0h * wr[d]: half-index change of a wrapping step
   FastDiv f_n0h, f_n1, f_n2, f_n0;
 };
 
@@ -476,6 +478,21 @@ __device__ __forceinline__ Site site_from_index(const Geom& g, uint32_t i) {
   return s;
 }
 
+// Half-index change of the step x -> x + S d-hat (S = +1 or -1), periodic.
+// For d >= 1 the step changes only the row; for d = 0 it changes x0 >> 1 by
+// 0 or +-1 (by the parity of x0), or wraps across the row.  Steps in
+// different directions change independent parts of the index, so the index of
+// x + a + b is h + step(a) + step(b).
+template <int D, int S> __device__ __forceinline__ int half_step(const Geom& g, const Site& x) {
+  if (D == 0) {
+    if (S > 0) return x.x0 + 1 == g.n[0] ? 1 - g.n0h : (x.x0 & 1);
+    return x.x0 == 0 ? g.n0h - 1 : (x.x0 & 1) - 1;
+  }
+  const int xd = D == 1 ? x.x1 : D == 2 ? x.x2 : x.x3;
+  if (S > 0) return xd + 1 == g.n[D] ? -g.hwr[D] : g.hst[D];
+  return xd == 0 ? g.hwr[D] : -g.hst[D];
+}
+
 // The two staple terms of Section 2 Eq. 11 for link (x, MU) and one NU != MU:
 // U_nu(x) U_mu(x+nu) U_nu(x+mu)^dagger + U_nu(x-nu)^dagger U_mu(x-nu)
 // U_nu(x-nu+mu).  U_nu(x) and U_nu(x-nu+mu) have the parity p of x; the four
@@ -495,6 +512,24 @@ __device__ __forceinline__ void staple_term(const Links<P>& L, const Geom& g, co
   const Quat<R> d = ldl<P, NC>(L, 2 * NU + q, h_mnu);   // U_nu(x-nu)
   const Quat<R> e = ldl<P, NC>(L, 2 * MU + q, h_mnu);   // U_mu(x-nu)
   const Quat<R> f = ldl<P, NC>(L, 2 * NU + p, h_mp);    // U_nu(x-nu+mu)
+  qacc_mul_nd(s, qmul(a, b), c);
+  qacc_mul(s, qmul_dn(d, e), f);
+}
+
+// staple_term with the neighbour indices from half-index steps (dmu = the
+// step x -> x + MU): the same loads and products in the same order.
+template <int P, int MU, int NU, bool NC>
+__device__ __forceinline__ void staple_term_steps(const Links<P>& L, const Geom& g, const Site& x, int h, int dmu,
+                                                  int p, Quat<typename Real<P>::T>& s) {
+  using R = typename Real<P>::T;
+  const int q = p ^ 1;
+  const int h_mnu = h + half_step<NU, -1>(g, x);
+  const Quat<R> a = ldl<P, NC>(L, 2 * NU + p, h);                          // U_nu(x)
+  const Quat<R> b = ldl<P, NC>(L, 2 * MU + q, h + half_step<NU, +1>(g, x)); // U_mu(x+nu)
+  const Quat<R> c = ldl<P, NC>(L, 2 * NU + q, h + dmu);                    // U_nu(x+mu)
+  const Quat<R> d = ldl<P, NC>(L, 2 * NU + q, h_mnu);                      // U_nu(x-nu)
+  const Quat<R> e = ldl<P, NC>(L, 2 * MU + q, h_mnu);                      // U_mu(x-nu)
+  const Quat<R> f = ldl<P, NC>(L, 2 * NU + p, h_mnu + dmu);                // U_nu(x-nu+mu)
   qacc_mul_nd(s, qmul(a, b), c);
   qacc_mul(s, qmul_dn(d, e), f);
 }
@@ -526,6 +561,9 @@ template <class R> __device__ __forceinline__ void staple_add(const StapleLinks<
 #ifndef SU2_STAPLE_LOADS_FIRST
 #define SU2_STAPLE_LOADS_FIRST 0
 #endif
+#ifndef SU2_STAPLE_STEPS
+#define SU2_STAPLE_STEPS 1
+#endif
 
 // Staple sum for link (x, MU) over the directions NU != MU selected by NMASK
 // (0xF: all, the heat bath; 0x7: the spatial ones, APE smearing).  With
@@ -551,6 +589,14 @@ __device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P>& L, c
     if (NMASK & (1 << N2)) staple_add(t2, s);
     return s;
   }
+  if (SU2_STAPLE_STEPS) {
+    const int dmu = half_step<MU, +1>(g, x);
+    if (MU != 0 && (NMASK & 1)) staple_term_steps<P, MU, 0, NC>(L, g, x, h, dmu, p, s);
+    if (MU != 1 && (NMASK & 2)) staple_term_steps<P, MU, 1, NC>(L, g, x, h, dmu, p, s);
+    if (MU != 2 && (NMASK & 4)) staple_term_steps<P, MU, 2, NC>(L, g, x, h, dmu, p, s);
+    if (MU != 3 && (NMASK & 8)) staple_term_steps<P, MU, 3, NC>(L, g, x, h, dmu, p, s);
+    return s;
+  }
   if (MU != 0 && (NMASK & 1)) staple_term<P, MU, 0, NC>(L, g, x, h, h_pmu, p, s);
   if (MU != 1 && (NMASK & 2)) staple_term<P, MU, 1, NC>(L, g, x, h, h_pmu, p, s);
   if (MU != 2 && (NMASK & 4)) staple_term<P, MU, 2, NC>(L, g, x, h, h_pmu, p, s);
@@ -567,14 +613,25 @@ __device__ __forceinline__ Quat<typename Real<P>::T> staple_split(const Links<P>
                                                                  int h, int p, Quat<typename Real<P>::T>& lower) {
   using R = typename Real<P>::T;
   Quat<R> s = qmake<R>(0, 0, 0, 0);
-  const int h_pmu = hidx(g, shifted<MU, +1>(g, x));
-  if (MU != 0) staple_term<P, MU, 0, NC>(L, g, x, h, h_pmu, p, s);
-  if (MU == 1) lower = s;
-  if (MU != 1) staple_term<P, MU, 1, NC>(L, g, x, h, h_pmu, p, s);
-  if (MU == 2) lower = s;
-  if (MU != 2) staple_term<P, MU, 2, NC>(L, g, x, h, h_pmu, p, s);
-  if (MU == 3) lower = s;
-  if (MU != 3) staple_term<P, MU, 3, NC>(L, g, x, h, h_pmu, p, s);
+  if (SU2_STAPLE_STEPS) {
+    const int dmu = half_step<MU, +1>(g, x);
+    if (MU != 0) staple_term_steps<P, MU, 0, NC>(L, g, x, h, dmu, p, s);
+    if (MU == 1) lower = s;
+    if (MU != 1) staple_term_steps<P, MU, 1, NC>(L, g, x, h, dmu, p, s);
+    if (MU == 2) lower = s;
+    if (MU != 2) staple_term_steps<P, MU, 2, NC>(L, g, x, h, dmu, p, s);
+    if (MU == 3) lower = s;
+    if (MU != 3) staple_term_steps<P, MU, 3, NC>(L, g, x, h, dmu, p, s);
+  } else {
+    const int h_pmu = hidx(g, shifted<MU, +1>(g, x));
+    if (MU != 0) staple_term<P, MU, 0, NC>(L, g, x, h, h_pmu, p, s);
+    if (MU == 1) lower = s;
+    if (MU != 1) staple_term<P, MU, 1, NC>(L, g, x, h, h_pmu, p, s);
+    if (MU == 2) lower = s;
+    if (MU != 2) staple_term<P, MU, 2, NC>(L, g, x, h, h_pmu, p, s);
+    if (MU == 3) lower = s;
+    if (MU != 3) staple_term<P, MU, 3, NC>(L, g, x, h, h_pmu, p, s);
+  }
   if (MU == 0) lower = qmake<R>(0, 0, 0, 0);
   return s;
 }

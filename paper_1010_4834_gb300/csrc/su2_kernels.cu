@@ -55,6 +55,10 @@ Geom make_geom(const int n[4]) {
   g.st[2] = n[1];
   g.st[3] = n[1] * n[2];
   for (int d = 0; d < 4; ++d) g.wr[d] = d ? g.st[d] * (n[d] - 1) : 0;
+  for (int d = 0; d < 4; ++d) {
+    g.hst[d] = d ? g.n0h * g.st[d] : 0;
+    g.hwr[d] = d ? g.n0h * g.wr[d] : 0;
+  }
   g.f_n0h = FastDiv((uint32_t)g.n0h);
   g.f_n1 = FastDiv((uint32_t)n[1]);
   g.f_n2 = FastDiv((uint32_t)n[2]);
