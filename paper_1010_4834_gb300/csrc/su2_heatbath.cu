@@ -31,8 +31,8 @@ namespace su2 {
 // spatial part, (NU,3) the space-time part) without another pass over the
 // links.
 // ---------------------------------------------------------------------------
-constexpr int kDeferCap = 512;
-constexpr int kDeferEvery = 8;
+constexpr int kDeferCap = 1024;
+constexpr int kDeferEvery = 32;
 
 template <class R, bool MEAS> struct Deferred {
   Quat<R> w;

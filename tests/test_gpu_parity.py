@@ -463,9 +463,9 @@ def test_sweep_measure_restart_and_launch_count():
 
 # The plaquette that sweep_measure takes from the odd-parity substeps of
 # mu = 1, 2, 3 against the plaquette kernel run after a plain sweep: every
-# branch of the update (first-trial accept, deferred trials, queue overflow,
-# capped link kept, Haar link at beta = 0, Creutz), each precision, a lattice
-# of several blocks with a ragged last one.  The measured sweeps must leave the
+# branch of the update (first-trial accept, deferred trials, capped link
+# kept, Haar link at beta = 0, Creutz; the queue overflow is covered on 48^4
+# below), each precision, a lattice of several blocks with a ragged last one.  The measured sweeps must leave the
 # same links as plain ones.
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-14), ("f32", 3e-6), ("f16q", 3e-6)])
 @pytest.mark.parametrize("beta,max_tries,sampler", [
@@ -491,13 +491,14 @@ def test_sweep_plaquette_matches_plaquette_kernel(prec, tol, beta, max_tries, sa
     b.close()
 
 
-@pytest.mark.parametrize("beta", [2.5, 0.05])
-def test_sweep_plaquette_full_size_grid(beta):
-    # 32^4: the substeps run the full persistent grid, several iterations per
-    # block; at beta 0.05 most first trials fail, the block queues overflow
-    # and some links exhaust their trials
-    a = Lattice((32, 32, 32, 32), beta, seed=43, start="hot", prec="f32")
-    b = Lattice((32, 32, 32, 32), beta, seed=43, start="hot", prec="f32")
+@pytest.mark.parametrize("n,beta", [(32, 2.5), (48, 0.05)])
+def test_sweep_plaquette_full_size_grid(n, beta):
+    # the substeps run the full persistent grid, several iterations per block;
+    # at beta 0.05 on 48^4 (17 iterations of 256 links per block) most first
+    # trials fail, the block queues overflow (1024 entries) and some links
+    # exhaust their trials
+    a = Lattice((n,) * 4, beta, seed=43, start="hot", prec="f32")
+    b = Lattice((n,) * 4, beta, seed=43, start="hot", prec="f32")
     hist = a.sweep_measure(2)
     b.sweep(2)
     np.testing.assert_allclose(hist[-1, :3], b.plaquette(), rtol=0, atol=2e-6)
