@@ -141,12 +141,13 @@ __device__ __forceinline__ uint4 philox(uint4 c, const RoundKeys& rk) {
 // ((x >> 9) + 1/2) 2^-23, exact in binary32 (23-bit resolution keeps the
 // value strictly below 1).  The FP32 value is built without an int-to-float
 // conversion: the bit pattern 0x3F800000 | (x >> 9) is 1 + k 2^-23 with
-// k = x >> 9, so subtracting 1 (exact) and adding 2^-24 (exact, k + 1/2 needs
-// 24 significant bits) gives (k + 1/2) 2^-23.
+// k = x >> 9, and subtracting 1 - 2^-24 (the largest float below 1) gives
+// (k + 1/2) 2^-23 in one exact subtraction (the operands are within a factor
+// of two of each other, and the difference needs 24 significant bits).
 template <class R> __device__ __forceinline__ R u01(uint32_t x);
 template <> __device__ __forceinline__ double u01<double>(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
 template <> __device__ __forceinline__ float u01<float>(uint32_t x) {
-  return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.0f) + 0x1p-24f;
+  return __uint_as_float(0x3F800000u | (x >> 9)) - 0x1.fffffep-1f;
 }
 
 // ---------------------------------------------------------------------------

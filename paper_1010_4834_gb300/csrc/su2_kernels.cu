@@ -633,6 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_wilson_plane_final(const double* p
 // ---------------------------------------------------------------------------
 constexpr int kWrtT = 16;  // T values per chunk
 
+
 template <int P, int RC, int NTH>
 __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, Geom g, int rmax, int tmax,
                                                       int ntc, int pad, double* partials) {
