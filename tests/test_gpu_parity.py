@@ -106,7 +106,7 @@ def substep_compare(dims, prec, beta, U0, mu, p, sweep, sampler="kp", max_tries=
     return st, (~ok).sum()
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16q"])
 @pytest.mark.parametrize("dims", SHAPES)
 def test_heatbath_substep(dims, prec):
     U0 = inputs.random_field(dims, 11)
@@ -224,8 +224,10 @@ def test_wilson_loops_both_chunkings_fp32_against_fp64_kernel():
     b.close()
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("n,alpha", [(0, 0.7), (1, 0.7), (3, 0.444), (25, 0.7)])
+# F16Q stores every smeared step in binary16, so it runs the short cases only
+@pytest.mark.parametrize("prec,n,alpha", [(p, n, a) for p in ("f64", "f32", "f16q")
+                                          for n, a in ((0, 0.7), (1, 0.7), (3, 0.444), (25, 0.7))
+                                          if not (p == "f16q" and n > 3)])
 def test_ape_and_smeared_wilson(prec, n, alpha):
     dims = (4, 6, 4, 6)
     U = inputs.random_field(dims, 31)
@@ -237,7 +239,7 @@ def test_ape_and_smeared_wilson(prec, n, alpha):
     ref = oracle.ape_smear(list(dims), as_stored(U, prec), alpha, n)
     got = lat.wilson_loops(4, 6, smeared=True)
     exp = oracle.wilson_loops(list(dims), ref, 4, 6)
-    tol = 1e-12 if prec == "f64" else 2e-5
+    tol = {"f64": 1e-12, "f32": 2e-5, "f16q": 5e-3}[prec]
     np.testing.assert_allclose(got, exp, atol=tol, rtol=0)
     # the chain itself is untouched
     np.testing.assert_allclose(lat.plaquette(), oracle.plaquette(list(dims), as_stored(U, prec)),
