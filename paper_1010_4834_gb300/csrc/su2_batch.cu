@@ -105,12 +105,13 @@ template <class R> struct BDeferred {
 // rejected links queued and finished by the whole block at the end.  Links
 // are read with coherent loads (other CTAs of the group wrote them before the
 // last barrier).
-template <int P, int MU>
-__device__ __forceinline__ void batch_substep(const Links<P>& L, const Geom& g, int p, int rank, int cpg,
+template <int P, int MU, int PAR>
+__device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geom& g, int rank, int cpg,
                                               uint32_t sweep, uint32_t tag, typename Real<P>::T beta,
                                               const HBParams& hp, BDeferred<typename Real<P>::T>* queue, int* qn) {
   using R = typename Real<P>::T;
   using M = Math<R>;
+  constexpr int p = PAR;
   const int vh = (int)g.vh;
   for (int base = rank * kBatchThreads; base < vh; base += cpg * kBatchThreads) {
     const int h = base + threadIdx.x;
@@ -180,9 +181,8 @@ __global__ void __launch_bounds__(kBatchThreads)
   for (int li = 0; li < pl.y; ++li) {
     const int l = order[pl.x + li];
     const Geom g = desc[l].g;
-    Links<P> L;
-    L.p = reinterpret_cast<decltype(L.p)>(desc[l].links);
-    L.vh = g.vh;
+    Links<P, true> L;
+    L.set(desc[l].links, g.vh);
     const R beta = (R)desc[l].beta;
     const uint32_t ltag = (uint32_t)l << 2;
     for (int sw = 0; sw < nsweeps; ++sw) {
@@ -190,11 +190,15 @@ __global__ void __launch_bounds__(kBatchThreads)
       for (int mu = 0; mu < 4; ++mu) {
         for (int p = 0; p < 2; ++p) {
           const uint32_t tag = (uint32_t)mu | ltag;
-          switch (mu) {
-            case 0: batch_substep<P, 0>(L, g, p, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-            case 1: batch_substep<P, 1>(L, g, p, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-            case 2: batch_substep<P, 2>(L, g, p, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-            default: batch_substep<P, 3>(L, g, p, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+          switch (2 * mu + p) {
+            case 0: batch_substep<P, 0, 0>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            case 1: batch_substep<P, 0, 1>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            case 2: batch_substep<P, 1, 0>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            case 3: batch_substep<P, 1, 1>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            case 4: batch_substep<P, 2, 0>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            case 5: batch_substep<P, 2, 1>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            case 6: batch_substep<P, 3, 0>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+            default: batch_substep<P, 3, 1>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
           }
           if (!group_barrier(bars + group, (unsigned)cpg, ctl, timeout_ns)) return;
         }

@@ -307,12 +307,26 @@ __device__ __forceinline__ int heatbath_draw(const Quat<R>& sigma, uint4 ctr, co
 // kernel writes the element); ldc() is a plain coherent load for kernels that
 // write links other blocks read after a grid barrier.
 // ---------------------------------------------------------------------------
-template <int P> struct Links;
+// CP selects the addressing: with CP a class starts at its own base pointer
+// c[cls] (kernel parameters), so a load is one multiply-add of the 32-bit
+// element index onto a constant; this is for kernels in which every class
+// index is a compile-time constant (a runtime index into c[] would force the
+// array into local memory).  Without CP a class starts at p + cls * vh.
+template <int P, bool CP = false> struct Links;
 
-template <> struct Links<kF64> {
+template <bool CP> struct Links<kF64, CP> {
   double2* p;     // 2 double2 per link
   int64_t vh;     // links per class
-  __device__ __forceinline__ const double2* at(int cls, int i) const { return p + 2 * (cls * vh + i); }
+  double2* c[8];  // start of each class (filled by set())
+  __host__ __device__ void set(void* base, int64_t n) {
+    p = static_cast<double2*>(base);
+    vh = n;
+    for (int k = 0; k < 8; ++k) c[k] = p + 2 * k * n;
+  }
+  __device__ __forceinline__ double2* at(int cls, int i) const {
+    if constexpr (CP) return c[cls] + 2 * (uint32_t)i;
+    else return p + 2 * (cls * vh + (uint32_t)i);
+  }
   __device__ __forceinline__ Quat<double> ld(int cls, int i) const {
     const double2* q = at(cls, i);
     const double2 a = __ldg(q), b = __ldg(q + 1);
@@ -324,7 +338,7 @@ template <> struct Links<kF64> {
     return qmake<double>(a.x, a.y, b.x, b.y);
   }
   __device__ __forceinline__ void st(int cls, int i, const Quat<double>& v) const {
-    double2* q = p + 2 * (cls * vh + i);
+    double2* q = at(cls, i);
     q[0] = make_double2(v.w, v.x);
     q[1] = make_double2(v.y, v.z);
   }
@@ -335,19 +349,29 @@ template <> struct Links<kF64> {
   }
 };
 
-template <> struct Links<kF32> {
+template <bool CP> struct Links<kF32, CP> {
   float4* p;
   int64_t vh;
+  float4* c[8];
+  __host__ __device__ void set(void* base, int64_t n) {
+    p = static_cast<float4*>(base);
+    vh = n;
+    for (int k = 0; k < 8; ++k) c[k] = p + k * n;
+  }
+  __device__ __forceinline__ float4* at(int cls, int i) const {
+    if constexpr (CP) return c[cls] + (uint32_t)i;
+    else return p + cls * vh + (uint32_t)i;
+  }
   __device__ __forceinline__ Quat<float> ld(int cls, int i) const {
-    const float4 a = __ldg(p + cls * vh + i);
+    const float4 a = __ldg(at(cls, i));
     return qmake<float>(a.x, a.y, a.z, a.w);
   }
   __device__ __forceinline__ Quat<float> ldc(int cls, int i) const {
-    const float4 a = p[cls * vh + i];
+    const float4 a = *at(cls, i);
     return qmake<float>(a.x, a.y, a.z, a.w);
   }
   __device__ __forceinline__ void st(int cls, int i, const Quat<float>& v) const {
-    p[cls * vh + i] = make_float4(v.w, v.x, v.y, v.z);
+    *at(cls, i) = make_float4(v.w, v.x, v.y, v.z);
   }
   __device__ __forceinline__ Quat<float> put(int cls, int i, const Quat<float>& v) const {
     st(cls, i, v);
@@ -356,11 +380,21 @@ template <> struct Links<kF32> {
 };
 
 // binary16 quaternion, re-normalised in FP32 on every load.
-template <> struct Links<kF16Q> {
+template <bool CP> struct Links<kF16Q, CP> {
   uint2* p;
   int64_t vh;
-  __device__ __forceinline__ Quat<float> ld(int cls, int i) const { return unpack(__ldg(p + cls * vh + i)); }
-  __device__ __forceinline__ Quat<float> ldc(int cls, int i) const { return unpack(p[cls * vh + i]); }
+  uint2* c[8];
+  __host__ __device__ void set(void* base, int64_t n) {
+    p = static_cast<uint2*>(base);
+    vh = n;
+    for (int k = 0; k < 8; ++k) c[k] = p + k * n;
+  }
+  __device__ __forceinline__ uint2* at(int cls, int i) const {
+    if constexpr (CP) return c[cls] + (uint32_t)i;
+    else return p + cls * vh + (uint32_t)i;
+  }
+  __device__ __forceinline__ Quat<float> ld(int cls, int i) const { return unpack(__ldg(at(cls, i))); }
+  __device__ __forceinline__ Quat<float> ldc(int cls, int i) const { return unpack(*at(cls, i)); }
   static __device__ __forceinline__ Quat<float> unpack(const uint2 a) {
     const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
     const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
@@ -375,17 +409,17 @@ template <> struct Links<kF16Q> {
     a.y = *reinterpret_cast<const uint32_t*>(&hi);
     return a;
   }
-  __device__ __forceinline__ void st(int cls, int i, const Quat<float>& v) const { p[cls * vh + i] = pack(v); }
+  __device__ __forceinline__ void st(int cls, int i, const Quat<float>& v) const { *at(cls, i) = pack(v); }
   // the stored value as a later load sees it: rounded to binary16, re-normalised
   __device__ __forceinline__ Quat<float> put(int cls, int i, const Quat<float>& v) const {
     const uint2 a = pack(v);
-    p[cls * vh + i] = a;
+    *at(cls, i) = a;
     return unpack(a);
   }
 };
 
-template <int P, bool NC>
-__device__ __forceinline__ Quat<typename Real<P>::T> ldl(const Links<P>& L, int cls, int i) {
+template <int P, bool NC, bool CP>
+__device__ __forceinline__ Quat<typename Real<P>::T> ldl(const Links<P, CP>& L, int cls, int i) {
   return NC ? L.ld(cls, i) : L.ldc(cls, i);
 }
 
@@ -498,8 +532,8 @@ template <int D, int S> __device__ __forceinline__ int half_step(const Geom& g, 
 // U_nu(x) U_mu(x+nu) U_nu(x+mu)^dagger + U_nu(x-nu)^dagger U_mu(x-nu)
 // U_nu(x-nu+mu).  U_nu(x) and U_nu(x-nu+mu) have the parity p of x; the four
 // singly shifted links have parity 1-p.
-template <int P, int MU, int NU, bool NC>
-__device__ __forceinline__ void staple_term(const Links<P>& L, const Geom& g, const Site& x, int h,
+template <int P, int MU, int NU, bool NC, bool CP>
+__device__ __forceinline__ void staple_term(const Links<P, CP>& L, const Geom& g, const Site& x, int h,
                                             int h_pmu, int p, Quat<typename Real<P>::T>& s) {
   using R = typename Real<P>::T;
   const int q = p ^ 1;
@@ -519,8 +553,8 @@ __device__ __forceinline__ void staple_term(const Links<P>& L, const Geom& g, co
 
 // staple_term with the neighbour indices from half-index steps (dmu = the
 // step x -> x + MU): the same loads and products in the same order.
-template <int P, int MU, int NU, bool NC>
-__device__ __forceinline__ void staple_term_steps(const Links<P>& L, const Geom& g, const Site& x, int h, int dmu,
+template <int P, int MU, int NU, bool NC, bool CP>
+__device__ __forceinline__ void staple_term_steps(const Links<P, CP>& L, const Geom& g, const Site& x, int h, int dmu,
                                                   int p, Quat<typename Real<P>::T>& s) {
   using R = typename Real<P>::T;
   const int q = p ^ 1;
@@ -538,8 +572,8 @@ __device__ __forceinline__ void staple_term_steps(const Links<P>& L, const Geom&
 // The six links of staple_term, loaded (no arithmetic).
 template <class R> struct StapleLinks { Quat<R> a, b, c, d, e, f; };
 
-template <int P, int MU, int NU, bool NC>
-__device__ __forceinline__ void staple_load(const Links<P>& L, const Geom& g, const Site& x, int h, int h_pmu,
+template <int P, int MU, int NU, bool NC, bool CP>
+__device__ __forceinline__ void staple_load(const Links<P, CP>& L, const Geom& g, const Site& x, int h, int h_pmu,
                                             int p, StapleLinks<typename Real<P>::T>& t) {
   const int q = p ^ 1;
   const Site xmnu = shifted<NU, -1>(g, x);
@@ -570,8 +604,8 @@ template <class R> __device__ __forceinline__ void staple_add(const StapleLinks<
 // (0xF: all, the heat bath; 0x7: the spatial ones, APE smearing).  With
 // SU2_STAPLE_LOADS_FIRST the loads of all directions are issued before any
 // product, so a warp has every load of the update in flight at once.
-template <int P, int MU, int NMASK, bool NC>
-__device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P>& L, const Geom& g,
+template <int P, int MU, int NMASK, bool NC, bool CP>
+__device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P, CP>& L, const Geom& g,
                                                            const Site& x, int h, int p) {
   using R = typename Real<P>::T;
   Quat<R> s = qmake<R>(0, 0, 0, 0);
@@ -609,8 +643,8 @@ __device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P>& L, c
 // with `lower` set to the partial sum over NU < MU.  Tr(U_MU(x) lower^dagger)/2
 // is the sum of the plaquettes in the planes (NU, MU), NU < MU, that contain
 // the link (Section 2, Eq. 12).
-template <int P, int MU, bool NC>
-__device__ __forceinline__ Quat<typename Real<P>::T> staple_split(const Links<P>& L, const Geom& g, const Site& x,
+template <int P, int MU, bool NC, bool CP>
+__device__ __forceinline__ Quat<typename Real<P>::T> staple_split(const Links<P, CP>& L, const Geom& g, const Site& x,
                                                                  int h, int p, Quat<typename Real<P>::T>& lower) {
   using R = typename Real<P>::T;
   Quat<R> s = qmake<R>(0, 0, 0, 0);
@@ -639,8 +673,8 @@ __device__ __forceinline__ Quat<typename Real<P>::T> staple_split(const Links<P>
 
 // One heat-bath update of link (x, MU): staple, draw, store (a capped link
 // is neither read nor written).  Returns the draw's trial count.
-template <int P, int MU, bool NC>
-__device__ __forceinline__ int heatbath_site(const Links<P>& L, const Geom& g, const Site& x, int h,
+template <int P, int MU, bool NC, bool CP>
+__device__ __forceinline__ int heatbath_site(const Links<P, CP>& L, const Geom& g, const Site& x, int h,
                                              int p, uint32_t sweep, const HBParams& hp,
                                              typename Real<P>::T beta) {
   using R = typename Real<P>::T;

@@ -57,10 +57,11 @@ __device__ __forceinline__ int finish_deferred(const Deferred<R, MEAS>& d, uint4
   return n;
 }
 
-template <int P, int MU, bool MEAS>
+template <int P, int MU, bool MEAS, int PAR>
 __global__ void __launch_bounds__(kThreads, Occ<P>::hb)
-    k_heatbath(Links<P> L, Geom g, int p, const uint32_t* sweep_base, uint32_t sweep_off,
+    k_heatbath(Links<P, true> L, Geom g, const uint32_t* sweep_base, uint32_t sweep_off,
                const __grid_constant__ HBParams hp, unsigned long long* stats, double* meas) {
+  constexpr int p = PAR;
   using R = typename Real<P>::T;
   using M = Math<R>;
   using Def = Deferred<R, MEAS>;
@@ -220,17 +221,22 @@ cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint
                             cudaStream_t st, double* meas, int* meas_blocks) {
   if (meas && (mu < 1 || parity != 1 || !meas_blocks)) return cudaErrorInvalidValue;
   SU2_DISPATCH(v.prec, SU2_DISPATCH_MU(mu, {
-    auto L = links_of<P>(v.links, v.g.vh);
+    // direction and parity are template parameters, so every class index in
+    // the kernel is a compile-time constant: per-class base pointers
+    auto L = links_of<P, true>(v.links, v.g.vh);
     if (meas) {
       if constexpr (MU >= 1) {
-        const int gr = grid_for(k_heatbath<P, MU, true>, v.g.vh);
+        const int gr = grid_for(k_heatbath<P, MU, true, 1>, v.g.vh);
         if (gr > kMeasStride) return cudaErrorInvalidConfiguration;
         *meas_blocks = gr;
-        k_heatbath<P, MU, true><<<gr, kThreads, 0, st>>>(L, v.g, parity, sweep_base, sweep_off, hp, stats, meas);
+        k_heatbath<P, MU, true, 1><<<gr, kThreads, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, stats, meas);
       }
+    } else if (parity == 0) {
+      const int gr = grid_for(k_heatbath<P, MU, false, 0>, v.g.vh);
+      k_heatbath<P, MU, false, 0><<<gr, kThreads, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, stats, nullptr);
     } else {
-      const int gr = grid_for(k_heatbath<P, MU, false>, v.g.vh);
-      k_heatbath<P, MU, false><<<gr, kThreads, 0, st>>>(L, v.g, parity, sweep_base, sweep_off, hp, stats, nullptr);
+      const int gr = grid_for(k_heatbath<P, MU, false, 1>, v.g.vh);
+      k_heatbath<P, MU, false, 1><<<gr, kThreads, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, stats, nullptr);
     }
   }));
   count_launches(1);

@@ -152,10 +152,9 @@ __device__ __forceinline__ void final_sum(const double* partials, int nblocks, d
 template <int P> struct Occ { static constexpr int hb = SU2_HB_MINB; };
 template <> struct Occ<kF64> { static constexpr int hb = 2; };
 
-template <int P> static Links<P> links_of(void* base, int64_t vh) {
-  Links<P> L;
-  L.p = reinterpret_cast<decltype(L.p)>(base);
-  L.vh = vh;
+template <int P, bool CP = false> static Links<P, CP> links_of(void* base, int64_t vh) {
+  Links<P, CP> L;
+  L.set(base, vh);
   return L;
 }
 

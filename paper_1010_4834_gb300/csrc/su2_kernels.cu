@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(kThreads) k_init(Links<P> L, Geom g, int start
 // Over-relaxation substep (Section 2, Eq. 10 with W = Sigma/|Sigma| for the
 // orientation of Eq. 11): U' = W U^dagger W keeps Tr(U Sigma^dagger).
 // ---------------------------------------------------------------------------
-template <int P, int MU>
-__global__ void __launch_bounds__(kThreads, Occ<P>::hb) k_overrelax(Links<P> L, Geom g, int p) {
+template <int P, int MU, int PAR>
+__global__ void __launch_bounds__(kThreads, Occ<P>::hb) k_overrelax(Links<P, true> L, Geom g) {
+  constexpr int p = PAR;
   using R = typename Real<P>::T;
   using M = Math<R>;
   const int stride = gridDim.x * blockDim.x;
@@ -875,9 +876,14 @@ cudaError_t launch_init(const LatticeView& v, int start, PhiloxKey key, uint32_t
 
 cudaError_t launch_overrelax(const LatticeView& v, int mu, int parity, cudaStream_t st) {
   SU2_DISPATCH(v.prec, SU2_DISPATCH_MU(mu, {
-    auto L = links_of<P>(v.links, v.g.vh);
-    const int gr = grid_for(k_overrelax<P, MU>, v.g.vh);
-    k_overrelax<P, MU><<<gr, kThreads, 0, st>>>(L, v.g, parity);
+    auto L = links_of<P, true>(v.links, v.g.vh);
+    if (parity == 0) {
+      const int gr = grid_for(k_overrelax<P, MU, 0>, v.g.vh);
+      k_overrelax<P, MU, 0><<<gr, kThreads, 0, st>>>(L, v.g);
+    } else {
+      const int gr = grid_for(k_overrelax<P, MU, 1>, v.g.vh);
+      k_overrelax<P, MU, 1><<<gr, kThreads, 0, st>>>(L, v.g);
+    }
   }));
   count_launches(1);
   return cudaGetLastError();

@@ -162,8 +162,7 @@ cudaError_t launch_static(const void* links, const Geom& g, double* scratch, int
   *blocks_needed = grid;
   if (grid > max_blocks) return cudaSuccess;
   Links<P> L;
-  L.p = reinterpret_cast<decltype(L.p)>(const_cast<void*>(links));
-  L.vh = g.vh;
+  L.set(const_cast<void*>(links), g.vh);
   k_plaquette_static<P><<<grid, kStaticThreads, 0, st>>>(L, g, scratch);
   return cudaGetLastError();
 }
