@@ -34,6 +34,12 @@ namespace su2 {
 constexpr int kDeferCap = 1024;
 constexpr int kDeferEvery = 32;
 
+template <class R> struct PlainAcc {
+  R s = R(0);
+  __device__ __forceinline__ void add(R v) { s += v; }
+  __device__ __forceinline__ double value() const { return (double)s; }
+};
+
 template <class R, bool MEAS> struct Deferred {
   Quat<R> w;
   R alpha;
@@ -71,7 +77,10 @@ __global__ void __launch_bounds__(kThreads, Occ<P>::hb)
   const uint32_t sweep = (sweep_base ? *sweep_base : 0u) + sweep_off;
   const uint32_t tag = (uint32_t)MU | hp.lattice_tag;
   unsigned int trials = 0, capped = 0, haar = 0;
-  Acc<R> plaq;  // MEAS: plaquettes of the planes (NU < MU, MU)
+  // MEAS: plaquettes of the planes (NU < MU, MU).  A plain sum: a thread adds
+  // vh / (grid size) terms of magnitude <= 2 (about 55 on 64^4), so FP32
+  // rounding stays near 1e-6 relative per thread before the FP64 block sums.
+  PlainAcc<R> plaq;
   if (threadIdx.x == 0) qn = 0;
   __syncthreads();
   const int vh = (int)g.vh;

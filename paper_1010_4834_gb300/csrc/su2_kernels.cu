@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) k_polyakov(Links<P> L, Geom g, doubl
 // backward.  blockIdx.y = parity.
 // ---------------------------------------------------------------------------
 template <int P, int MU, int NU>
-__device__ __forceinline__ void ape_pair(const Links<P>& L, const Geom& g, const Site& x, int p,
+__device__ __forceinline__ void ape_pair(const Links<P, true>& L, const Geom& g, const Site& x, int p,
                                          const Quat<typename Real<P>::T>& umu, const Quat<typename Real<P>::T>& unu,
                                          Quat<typename Real<P>::T>& smu, Quat<typename Real<P>::T>& snu) {
   using R = typename Real<P>::T;
@@ -279,7 +279,7 @@ __device__ __forceinline__ void ape_pair(const Links<P>& L, const Geom& g, const
 }
 
 template <int P>
-__device__ __forceinline__ void ape_store(const Links<P>& dst, int cls, int h, const Quat<typename Real<P>::T>& u,
+__device__ __forceinline__ void ape_store(const Links<P, true>& dst, int cls, int h, const Quat<typename Real<P>::T>& u,
                                           const Quat<typename Real<P>::T>& sig, typename Real<P>::T c0,
                                           typename Real<P>::T c1) {
   using R = typename Real<P>::T;
@@ -292,12 +292,13 @@ __device__ __forceinline__ void ape_store(const Links<P>& dst, int cls, int h, c
 #ifndef SU2_APE3_MINB
 #define SU2_APE3_MINB 3
 #endif
-template <int P>
-__global__ void __launch_bounds__(kThreads, P == kF64 ? 2 : SU2_APE3_MINB) k_ape(Links<P> src, Links<P> dst, Geom g, double alpha_d) {
+// The sites of parity PAR (a template parameter, so every class index is a
+// compile-time constant for the per-class base pointers).
+template <int P, int PAR>
+__device__ __forceinline__ void ape_sites(const Links<P, true>& src, const Links<P, true>& dst, const Geom& g,
+                                          typename Real<P>::T c0, typename Real<P>::T c1) {
   using R = typename Real<P>::T;
-  const R alpha = (R)alpha_d;
-  const R c0 = R(1) - alpha, c1 = R(0.25) * alpha;
-  const int p = blockIdx.y;
+  constexpr int p = PAR;
   const int vh = (int)g.vh;
   const int stride = gridDim.x * blockDim.x;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < vh; h += stride) {
@@ -311,6 +312,16 @@ __global__ void __launch_bounds__(kThreads, P == kF64 ? 2 : SU2_APE3_MINB) k_ape
     ape_store<P>(dst, 2 + p, h, u1, s1, c0, c1);
     ape_store<P>(dst, 4 + p, h, u2, s2, c0, c1);
   }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads, P == kF64 ? 2 : SU2_APE3_MINB)
+    k_ape(Links<P, true> src, Links<P, true> dst, Geom g, double alpha_d) {
+  using R = typename Real<P>::T;
+  const R alpha = (R)alpha_d;
+  const R c0 = R(1) - alpha, c1 = R(0.25) * alpha;
+  if (blockIdx.y == 0) ape_sites<P, 0>(src, dst, g, c0, c1);
+  else ape_sites<P, 1>(src, dst, g, c0, c1);
 }
 
 template <int P>
@@ -912,8 +923,8 @@ cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t
 
 cudaError_t launch_ape(const LatticeView& src, void* dst, double alpha, cudaStream_t st) {
   SU2_DISPATCH(src.prec, {
-    auto S = links_of<P>(src.links, src.g.vh);
-    auto D = links_of<P>(dst, src.g.vh);
+    auto S = links_of<P, true>(src.links, src.g.vh);
+    auto D = links_of<P, true>(dst, src.g.vh);
     // two y-slices (one per parity) share the machine
     int gx = grid_for(k_ape<P>, 2 * src.g.vh) / 2;
     if (gx < 1) gx = 1;
