@@ -315,9 +315,19 @@ __device__ __forceinline__ int heatbath_draw(const Quat<R>& sigma, uint4 ctr, co
 template <int P, bool CP = false> struct Links;
 
 template <bool CP> struct Links<kF64, CP> {
+  using E = double2;
   double2* p;     // 2 double2 per link
   int64_t vh;     // links per class
   double2* c[8];  // start of each class (filled by set())
+  // start of class cls, and link i of the class that starts at b
+  __device__ __forceinline__ double2* cls_base(int cls) const {
+    if constexpr (CP) return c[cls];
+    else return p + 2 * cls * vh;
+  }
+  static __device__ __forceinline__ Quat<double> ldp(const double2* b, uint32_t i) {
+    const double2 a = __ldg(b + 2 * i), d = __ldg(b + 2 * i + 1);
+    return qmake<double>(a.x, a.y, d.x, d.y);
+  }
   __host__ __device__ void set(void* base, int64_t n) {
     p = static_cast<double2*>(base);
     vh = n;
@@ -350,9 +360,18 @@ template <bool CP> struct Links<kF64, CP> {
 };
 
 template <bool CP> struct Links<kF32, CP> {
+  using E = float4;
   float4* p;
   int64_t vh;
   float4* c[8];
+  __device__ __forceinline__ float4* cls_base(int cls) const {
+    if constexpr (CP) return c[cls];
+    else return p + cls * vh;
+  }
+  static __device__ __forceinline__ Quat<float> ldp(const float4* b, uint32_t i) {
+    const float4 a = __ldg(b + i);
+    return qmake<float>(a.x, a.y, a.z, a.w);
+  }
   __host__ __device__ void set(void* base, int64_t n) {
     p = static_cast<float4*>(base);
     vh = n;
@@ -381,9 +400,15 @@ template <bool CP> struct Links<kF32, CP> {
 
 // binary16 quaternion, re-normalised in FP32 on every load.
 template <bool CP> struct Links<kF16Q, CP> {
+  using E = uint2;
   uint2* p;
   int64_t vh;
   uint2* c[8];
+  __device__ __forceinline__ uint2* cls_base(int cls) const {
+    if constexpr (CP) return c[cls];
+    else return p + cls * vh;
+  }
+  static __device__ __forceinline__ Quat<float> ldp(const uint2* b, uint32_t i) { return unpack(__ldg(b + i)); }
   __host__ __device__ void set(void* base, int64_t n) {
     p = static_cast<uint2*>(base);
     vh = n;

@@ -31,7 +31,10 @@ namespace su2 {
 // spatial part, (NU,3) the space-time part) without another pass over the
 // links.
 // ---------------------------------------------------------------------------
-constexpr int kDeferCap = 1024;
+// Queue capacity: the plaquette-summing variant's entries are larger (they
+// carry the partial staple), so it keeps fewer and leaves the SM's L1 share
+// of the shared-memory carveout about the same.
+template <bool MEAS> struct DeferCap { static constexpr int value = MEAS ? 512 : 1024; };
 constexpr int kDeferEvery = 32;
 
 template <class R> struct PlainAcc {
@@ -71,6 +74,7 @@ __global__ void __launch_bounds__(kThreads, Occ<P>::hb)
   using R = typename Real<P>::T;
   using M = Math<R>;
   using Def = Deferred<R, MEAS>;
+  constexpr int kDeferCap = DeferCap<MEAS>::value;
   __shared__ Def queue[kDeferCap];
   __shared__ int qn;
   const R beta = (R)hp.beta;

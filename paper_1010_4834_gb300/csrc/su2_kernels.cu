@@ -212,9 +212,10 @@ __global__ void __launch_bounds__(kThreads) k_plaquette(Links<P> L, Geom g, doub
 // chunk of 8 links are issued before the products that consume them.
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_polyakov(Links<P> L, Geom g, double* partials,
+__global__ void __launch_bounds__(kThreads) k_polyakov(Links<P, true> L, Geom g, double* partials,
                                                        unsigned int* counter, double* out) {
   using R = typename Real<P>::T;
+  using LT = Links<P, true>;
   Acc<R> acc;
   const int nsig = g.n[0] * g.n[1] * g.n[2];
   const int nsig_h = nsig / 2;
@@ -223,17 +224,21 @@ __global__ void __launch_bounds__(kThreads) k_polyakov(Links<P> L, Geom g, doubl
   for (int xs = blockIdx.x * blockDim.x + threadIdx.x; xs < nsig; xs += stride) {
     const Site x = site_from_index(g, (uint32_t)xs);
     const int px = parity(x);
-    const int hh = xs >> 1;
+    const uint32_t hh = (uint32_t)(xs >> 1);
+    // the time links of x alternate between the two parity classes: b0 holds
+    // those at even t, b1 those at odd t
+    const typename LT::E* b0 = px ? L.cls_base(7) : L.cls_base(6);
+    const typename LT::E* b1 = px ? L.cls_base(6) : L.cls_base(7);
     Quat<R> pr = qone<R>();
     int t = 0;
     for (; t + 8 <= nt; t += 8) {
       Quat<R> u[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) u[j] = L.ld(6 + ((px + t + j) & 1), hh + nsig_h * (t + j));
+      for (int j = 0; j < 8; ++j) u[j] = LT::ldp((j & 1) ? b1 : b0, hh + (uint32_t)nsig_h * (t + j));
 #pragma unroll
       for (int j = 0; j < 8; ++j) pr = qmul(pr, u[j]);
     }
-    for (; t < nt; ++t) pr = qmul(pr, L.ld(6 + ((px + t) & 1), hh + nsig_h * t));
+    for (; t < nt; ++t) pr = qmul(pr, LT::ldp((t & 1) ? b1 : b0, hh + (uint32_t)nsig_h * t));
     acc.add(pr.w);
   }
   double v[1] = {acc.value()};
@@ -912,7 +917,7 @@ cudaError_t launch_plaquette(const LatticeView& v, const Scratch& s, cudaStream_
 
 cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t st) {
   SU2_DISPATCH(v.prec, {
-    auto L = links_of<P>(v.links, v.g.vh);
+    auto L = links_of<P, true>(v.links, v.g.vh);
     const int64_t nsig = 2 * v.g.vh / v.g.n[3];
     const int gr = grid_for(k_polyakov<P>, nsig);
     k_polyakov<P><<<gr, kThreads, 0, st>>>(L, v.g, s.partials, s.counter, s.out);
