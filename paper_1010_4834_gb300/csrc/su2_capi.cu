@@ -562,9 +562,26 @@ extern "C" int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smea
   return fetch_out(h, Rmax * Tmax, out);
 }
 
+// The device-visible address of page-locked host memory (cudaHostAlloc,
+// cudaHostRegister: the conversion kernels then read or write it directly
+// over the host link), or NULL for pageable memory.
+static void* host_mapped(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Sites [first, first + count) in canonical FP64 order into host[16 * count].
 static int copy_sites_out(su2_lattice* h, int64_t first, int64_t count, double* host) {
   DeviceGuard dg(h->device);
+  if (void* d = count > 0 ? host_mapped(host) : nullptr) {
+    SU2_CU(launch_to_canonical(view(h), static_cast<double*>(d), first, count, h->stream));
+    SU2_CU(cudaStreamSynchronize(h->stream));
+    return SU2_OK;
+  }
   for (int64_t k = 0; k < count; k += h->staging_sites) {
     const int64_t ns = count - k < h->staging_sites ? count - k : h->staging_sites;
     SU2_CU(launch_to_canonical(view(h), h->staging, first + k, ns, h->stream));
@@ -596,11 +613,15 @@ extern "C" int su2_set_links(su2_lattice* h, const double* host) {
   if (!h || !host) return fail(SU2_EINVAL, "NULL argument");
   DeviceGuard dg(h->device);
   const int64_t V = 2 * h->g.vh;
-  for (int64_t s0 = 0; s0 < V; s0 += h->staging_sites) {
-    const int64_t ns = V - s0 < h->staging_sites ? V - s0 : h->staging_sites;
-    SU2_CU(cudaMemcpyAsync(h->staging, host + 16 * s0, (size_t)ns * 16 * sizeof(double),
-                           cudaMemcpyHostToDevice, h->stream));
-    SU2_CU(launch_from_canonical(view(h), h->staging, s0, ns, h->stream));
+  if (const void* d = host_mapped(host)) {
+    SU2_CU(launch_from_canonical(view(h), static_cast<const double*>(d), 0, V, h->stream));
+  } else {
+    for (int64_t s0 = 0; s0 < V; s0 += h->staging_sites) {
+      const int64_t ns = V - s0 < h->staging_sites ? V - s0 : h->staging_sites;
+      SU2_CU(cudaMemcpyAsync(h->staging, host + 16 * s0, (size_t)ns * 16 * sizeof(double),
+                             cudaMemcpyHostToDevice, h->stream));
+      SU2_CU(launch_from_canonical(view(h), h->staging, s0, ns, h->stream));
+    }
   }
   SU2_CU(cudaStreamSynchronize(h->stream));
   h->smeared = 0;

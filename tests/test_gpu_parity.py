@@ -84,6 +84,32 @@ def test_set_get_roundtrip(prec):
     lat.close()
 
 
+@pytest.mark.parametrize("prec", ["f64", "f16q"])
+def test_pinned_host_buffers_take_the_direct_path(prec):
+    # page-locked buffers are read and written by the conversion kernels
+    # directly; the result must equal the staged copy of pageable memory,
+    # also for a site range in the middle of the buffer
+    import torch
+    dims = (8, 6, 4, 10)
+    U = inputs.random_field(dims, 17)
+    V = int(np.prod(dims))
+    pinned = torch.from_numpy(U.copy()).pin_memory()
+    a = Lattice(dims, 2.0, prec=prec)
+    b = Lattice(dims, 2.0, prec=prec)
+    a.set_links(pinned.numpy())
+    b.set_links(U)
+    out = torch.empty((V, 4, 4), dtype=torch.float64).pin_memory()
+    a.get_links(out.numpy())
+    np.testing.assert_array_equal(out.numpy(), b.get_links())
+    part = torch.empty((100, 4, 4), dtype=torch.float64).pin_memory()
+    from paper_1010_4834_gb300 import _lib
+    from paper_1010_4834_gb300.lattice import _dptr
+    _lib.check(_lib.load().su2_get_sites(a._h, 777, 100, _dptr(part.numpy())))
+    np.testing.assert_array_equal(part.numpy(), b.get_sites(777, 100))
+    a.close()
+    b.close()
+
+
 # ---------------------------------------------------------------------------
 def substep_compare(dims, prec, beta, U0, mu, p, sweep, sampler="kp", max_tries=64, seed=7):
     lat = Lattice(dims, beta, seed=seed, prec=prec)
