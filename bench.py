@@ -153,18 +153,33 @@ def timed_sweeps(torch, lat, n, reps=3):
 
 
 def substep_launch_seconds(torch, lat, sweeps=4):
-    """Average CUDA-event duration of one heat-bath substep launch."""
+    """Average duration of one heat-bath substep launch: one CUDA-event pair
+    around 8 * sweeps substeps launched back to back on the lattice's stream
+    (the way a sweep runs them), and, for comparison, the mean of the same
+    launches each bracketed by its own events with the stream idle between
+    them (which adds the launch latency to every launch)."""
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for sw in range(sweeps):
+        for mu in range(4):
+            for p in range(2):
+                lat.substep(mu, p, 1000 + sw)
+    b.record()
+    torch.cuda.synchronize()
+    n = 8 * sweeps
+    back_to_back = a.elapsed_time(b) / 1e3 / n
     times = []
     for sw in range(sweeps):
         for mu in range(4):
             for p in range(2):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record()
-                lat.substep(mu, p, 1000 + sw)
+                lat.substep(mu, p, 2000 + sw)
                 b.record()
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(b) / 1e3)
-    return statistics.mean(times), len(times)
+    return back_to_back, n, statistics.mean(times)
 
 
 def reduce_over_ranks(dist, elapsed, launches, device):
@@ -290,7 +305,7 @@ def run_gpu_on_stream(args):
     plaq_last = float(hist[-1, 0])
 
     # roofline of the heat-bath substep (FP32: 8 links of 16 B per update)
-    t_launch, n_launch = substep_launch_seconds(torch, lat)
+    t_launch, n_launch, t_isolated = substep_launch_seconds(torch, lat)
     upd_launch = V // 2
     alg_bytes = 8 * 16 * upd_launch
     peaks, peak_kind = measured_peaks()
@@ -299,7 +314,9 @@ def run_gpu_on_stream(args):
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
                 "peak_kind": peak_kind, "traffic": profiled_traffic(upd_launch),
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_us": round(t_launch * 1e6, 2),
-                "launches_timed": n_launch, "updates_per_s_in_kernel": upd_launch / t_launch}
+                "launches_timed": n_launch, "timing": "one event pair around %d back-to-back launches" % n_launch,
+                "launch_us_isolated": round(t_isolated * 1e6, 2),
+                "updates_per_s_in_kernel": upd_launch / t_launch}
 
     # end to end through the public API from a host configuration in pinned memory
     host_cfg = torch.empty((V, 4, 4), dtype=torch.float64, pin_memory=True)
