@@ -106,3 +106,24 @@ def test_batched_ensemble_against_single_lattices():
         ref = chain_history(d, be, "f64", 808 + i, 200, 2000)[:, 0]
         ok, info = agree(binned(mine), binned(ref))
         assert ok, (d, info)
+
+
+def test_finite_temperature_scan_reduced_precisions_match_fp64():
+    """The 32^3 x 4 scan at 16 couplings in [2.2, 2.6] (cold start, 1000
+    sweeps each, the first 300 dropped): FP32 and F16Q plaquette and |Polyakov loop| against
+    the FP64 ensemble at every coupling.  With 64 comparisons a 3-sigma cut
+    would fail by chance about one run in six, so each deviation must stay
+    within 4 combined errors and their mean square near 1; and |L| must show
+    the transition (small at 2.2, large at 2.6)."""
+    from paper_1010_4834_gb300.ensemble import deviation, scan
+    res = scan()
+    z = []
+    for k, (beta, p64, l64) in enumerate(res["f64"]):
+        for prec in ("f32", "f16q"):
+            _, p, l = res[prec][k]
+            z += [deviation(p, p64), deviation(l, l64)]
+    z = np.array(z)
+    assert np.all(np.abs(z) < 4), z
+    assert np.mean(z ** 2) < 2.0, np.mean(z ** 2)
+    l_lo, l_hi = res["f64"][0][2][0], res["f64"][-1][2][0]
+    assert l_lo < 0.1 < 0.2 < l_hi, (l_lo, l_hi)
