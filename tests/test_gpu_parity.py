@@ -318,12 +318,14 @@ def test_argument_and_state_errors():
     lat = Lattice((4, 4, 4, 4), 2.0, prec="f32")
     for bad in [lambda: lat.wilson_loops(5, 2), lambda: lat.wilson_loops(2, 5), lambda: lat.wilson_loops(0, 1),
                 lambda: lat.ape_smear(1.0, 1), lambda: lat.ape_smear(0.5, -1), lambda: lat.sweep(-1),
-                lambda: lat.substep(4, 0, 0), lambda: lat.set_options(0, "kp"), lambda: lat.set_beta(-1.0)]:
+                lambda: lat.substep(4, 0, 0), lambda: lat.set_options(0, "kp"), lambda: lat.set_beta(-1.0),
+                lambda: lat.get_sites(-1, 1), lambda: lat.get_sites(250, 7), lambda: lat.layout_compare(0)]:
         with pytest.raises(SU2Error) as e:
             bad()
         assert e.value.code == 1
     with pytest.raises(SU2Error):
         Lattice((4, 4, 4, 5), 2.0)
+    assert lat.get_sites(256, 0).shape == (0, 4, 4)      # an empty range at the end is valid
     lat.close()
 
 
