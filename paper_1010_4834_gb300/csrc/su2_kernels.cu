@@ -635,17 +635,18 @@ __global__ void __launch_bounds__(kThreads) k_wilson_plane_final(const double* p
 // ... U_t(a, t+T-1), the loop of Eq. 18 at (a, t) is
 //   W = (1/2) Tr[S_R(a,t) T_T(a+R,t) S_R(a,t+T)^dag T_T(a,t)^dag]
 //     = (F . Q),  F = S_R(a,t) T_T(a+R,t),  Q = T_T(a,t) S_R(a,t+T).
-// A thread owns one site of a plane staged in shared memory and holds F for
-// RC consecutive R in registers.  Stepping T by one multiplies each F by one
+// A thread owns one site of a plane (or of a band of its time slices, when
+// the whole plane does not fit) staged in shared memory and holds F for RC
+// consecutive R in registers.  Stepping T by one multiplies each F by one
 // time link and D = T_T(a,t) by one; Q is then rebuilt along R from D with
 // one spatial link per R.  That is two quaternion products and a dot product
 // per (R, T), where extending every line per (R, T) costs four to five.
 // blockIdx.y = (R chunk, T chunk); chunks after the first start from prefix
 // products.  Plane rows are stored with `pad` extra columns repeating the
 // first ones, so the lines along MU need no periodic wrap test.  Loop values
-// go through a transposing warp reduction into per-warp FP32 sums of the
-// plane, which are folded into the block's FP64 totals after each plane in a
-// fixed order (no atomics); per-block sums go to `partials` in a fixed layout
+// go through a transposing warp reduction into per-warp sums of the work
+// unit (FP32 or FP64, the arithmetic's precision), which are folded into the
+// block's FP64 totals after each unit in a fixed order (no atomics); per-block sums go to `partials` in a fixed layout
 // for k_wilson_rt_final.
 // ---------------------------------------------------------------------------
 constexpr int kWrtT = 16;  // T values per chunk
@@ -653,43 +654,55 @@ constexpr int kWrtT = 16;  // T values per chunk
 
 template <int P, int RC, int NTH>
 __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, Geom g, int rmax, int tmax,
-                                                      int ntc, int pad, double* partials) {
+                                                      int ntc, int pad, int tile, double* partials) {
   using R = typename Real<P>::T;
   static_assert(RC == 8 || RC == 16, "R chunk must be 8 or 16");
   constexpr int NS = RC * kWrtT;  // (R, T) slots of one chunk
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double acc[NS];               // block totals; slot k belongs to thread k
-  __shared__ float wacc[NTH / 32][NS];     // one plane's sums per warp
+  __shared__ R wacc[NTH / 32][NS];         // one work unit's sums per warp (in the arithmetic's precision)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rc = blockIdx.y / ntc, tc = blockIdx.y - (blockIdx.y / ntc) * ntc;
   const int r0 = rc * RC, t0 = tc * kWrtT;
   const int nR = min(RC, rmax - r0), nT = min(kWrtT, tmax - t0);
   const int nt = g.n[3];
+  // a work unit is `tile` consecutive time slices of one plane.  A whole
+  // plane (tile == nt) is staged once, rows read modulo nt; a band of slices
+  // stages rows tstart .. tstart + nrows - 1 (mod nt), enough for every line
+  // its sites start (T up to ntc * kWrtT beyond the last slice), and reads
+  // them without a wrap
+  const bool whole = tile >= nt;
+  const int ntiles = whole ? 1 : (nt + tile - 1) / tile;
+  const int nrows = whole ? nt : tile + ntc * kWrtT;
+  const int wrap_at = whole ? nt : 0x7fffffff;
   for (int i = threadIdx.x; i < NS; i += NTH) acc[i] = 0.0;
-  for (int i = threadIdx.x; i < (NTH / 32) * NS; i += NTH) (&wacc[0][0])[i] = 0.f;
+  for (int i = threadIdx.x; i < (NTH / 32) * NS; i += NTH) (&wacc[0][0])[i] = R(0);
   const int ntr0 = g.n[1] * g.n[2], ntr1 = g.n[0] * g.n[2], ntr2 = g.n[0] * g.n[1];
-  const int nplanes = ntr0 + ntr1 + ntr2;
-  for (int pl = blockIdx.x; pl < nplanes; pl += gridDim.x) {
+  const int nunits = (ntr0 + ntr1 + ntr2) * ntiles;
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int pl = u / ntiles, tstart = (u - pl * ntiles) * tile;
     const int mu = pl < ntr0 ? 0 : (pl < ntr0 + ntr1 ? 1 : 2);
     const int tr = pl - (mu == 0 ? 0 : (mu == 1 ? ntr0 : ntr0 + ntr1));
     const int nm = mu == 0 ? g.n[0] : (mu == 1 ? g.n[1] : g.n[2]);
-    const int np = nm * nt;
+    const int tn = min(tile, nt - tstart);  // slices whose sites this unit owns
+    const int np = nm * tn;
     // rows of W = nm + pad columns: column c holds plane column c mod nm, so
-    // every line a, a+1, ..., a + pad - 1 is read without a wrap test
+    // every line a, a+1, ..., a + pad - 1 is read without a wrap test; row r
+    // holds time slice tstart + r (mod nt), so lines along t need none either
     const int W = nm + pad;
-    Quat<R>* us = reinterpret_cast<Quat<R>*>(smem_raw);   // us[c + W t] = U_mu(c mod nm, t)
-    Quat<R>* ut = us + W * nt;                            // ut[c + W t] = U_t(c mod nm, t)
+    Quat<R>* us = reinterpret_cast<Quat<R>*>(smem_raw);   // us[c + W r] = U_mu(c mod nm, tstart + r)
+    Quat<R>* ut = us + W * nrows;                         // ut[c + W r] = U_t(c mod nm, tstart + r)
     const int n1st = mu == 0 ? g.n[1] : g.n[0];
     const int c1 = tr % n1st, c2 = tr / n1st;
-    __syncthreads();  // the previous plane's readers and the warp-sum fold are done
-    for (int i = threadIdx.x; i < W * nt; i += NTH) {
-      const int c = i % W, t = i / W;
+    __syncthreads();  // the previous unit's readers and the warp-sum fold are done
+    for (int i = threadIdx.x; i < W * nrows; i += NTH) {
+      const int c = i % W, r = i / W;
       const int a = c % nm;
       Site y;
       y.x0 = mu == 0 ? a : c1;
       y.x1 = mu == 0 ? c1 : (mu == 1 ? a : c2);
       y.x2 = mu == 2 ? a : c2;
-      y.x3 = t;
+      y.x3 = (tstart + r) % nt;
       y.row = y.x1 + g.n[1] * (y.x2 + g.n[2] * y.x3);
       const int h = hidx(g, y), par = parity(y);
       us[i] = Ls.ld(2 * mu + par, h);
@@ -699,7 +712,7 @@ __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, 
     for (int base = 0; base < np; base += NTH) {
       const int i = base + threadIdx.x;
       const bool valid = i < np;
-      const int a = valid ? i % nm : 0, t = valid ? i / nm : 0;
+      const int a = valid ? i % nm : 0, t = valid ? i / nm : 0;   // t: local row of the site
       // F[k] = S_{r0+k+1}(a, t) T_{t0}(a+r0+k+1, t),  D = T_{t0}(a, t)
       Quat<R> F[RC];
       {
@@ -713,15 +726,13 @@ __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, 
         }
       }
       Quat<R> D = qone<R>();
-      int tt = t;                                   // t + T - 1 for the next T
+      int tt = t;                                   // row of t + T - 1 for the next T
       for (int j = 0; j < t0; ++j) {
         D = qmul(D, ut[a + W * tt]);
-        if (t0 > 0) {
-          const Quat<R>* row = ut + a + r0 + 1 + W * tt;
+        const Quat<R>* row = ut + a + r0 + 1 + W * tt;
 #pragma unroll
-          for (int k = 0; k < RC; ++k) F[k] = qmul(F[k], row[k]);
-        }
-        tt = tt + 1 == nt ? 0 : tt + 1;
+        for (int k = 0; k < RC; ++k) F[k] = qmul(F[k], row[k]);
+        tt = tt + 1 == wrap_at ? 0 : tt + 1;
       }
       for (int j = 0; j < nT; ++j) {             // T = t0 + j + 1
         D = qmul(D, ut[a + W * tt]);
@@ -730,7 +741,7 @@ __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, 
 #pragma unroll
           for (int k = 0; k < RC; ++k) F[k] = qmul(F[k], row[k]);
         }
-        tt = tt + 1 == nt ? 0 : tt + 1;           // t + T
+        tt = tt + 1 == wrap_at ? 0 : tt + 1;     // row of t + T
         const Quat<R>* row = us + a + W * tt;
         Quat<R> Q = D;
         for (int k = 0; k < r0; ++k) Q = qmul(Q, row[k]);
@@ -761,17 +772,17 @@ __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, 
           }
         }
         // owner lanes hold distinct R slots: plain read-modify-write
-        if ((lane & (32 / RC - 1)) == 0 && lo < nR) wacc[warp][lo * kWrtT + j] += (float)val[0];
+        if ((lane & (32 / RC - 1)) == 0 && lo < nR) wacc[warp][lo * kWrtT + j] += val[0];
       }
     }
     __syncthreads();
-    // fold the warps' plane sums into the block totals in a fixed order
+    // fold the warps' sums into the block totals in a fixed order
     for (int k = threadIdx.x; k < NS; k += NTH) {
       double t = 0.0;
 #pragma unroll
       for (int w = 0; w < NTH / 32; ++w) {
         t += (double)wacc[w][k];
-        wacc[w][k] = 0.f;
+        wacc[w][k] = R(0);
       }
       acc[k] += t;
     }
@@ -1009,8 +1020,8 @@ constexpr int kWilsonRtThreads = 512;
 constexpr int kWilsonRtSmemMax = 208 * 1024;
 
 template <int P, int RC>
-static cudaError_t launch_wilson_rt_rc(const LatticeView& v, const void* spatial, int rmax, int tmax, int smem,
-                                       const Scratch& s, cudaStream_t st) {
+static cudaError_t launch_wilson_rt_rc(const LatticeView& v, const void* spatial, int rmax, int tmax, int tile,
+                                       int smem, const Scratch& s, cudaStream_t st) {
   constexpr int NTH = kWilsonRtThreads;
   static bool attr_set[64] = {false};
   int dev = 0;
@@ -1026,16 +1037,17 @@ static cudaError_t launch_wilson_rt_rc(const LatticeView& v, const void* spatial
   if (per_sm < 1) per_sm = 1;
   const int nrc = (rmax + RC - 1) / RC, ntc = (tmax + kWrtT - 1) / kWrtT;
   const int nchunks = nrc * ntc;
-  const int nplanes = v.g.n[1] * v.g.n[2] + v.g.n[0] * v.g.n[2] + v.g.n[0] * v.g.n[1];
+  const int ntiles = (v.g.n[3] + tile - 1) / tile;
+  const int64_t nunits = (int64_t)(v.g.n[1] * v.g.n[2] + v.g.n[0] * v.g.n[2] + v.g.n[0] * v.g.n[1]) * ntiles;
   int64_t gx = ((int64_t)device_info().sms * per_sm + nchunks - 1) / nchunks;
-  if (gx > nplanes) gx = nplanes;
+  if (gx > nunits) gx = nunits;
   const int64_t cap = (int64_t)kScratchPartials / (RC * kWrtT) / nchunks;
   if (gx > cap) gx = cap;
   if (gx < 1) gx = 1;
   auto Lt = links_of<P>(v.links, v.g.vh);
   auto Ls = links_of<P>(const_cast<void*>(spatial), v.g.vh);
   k_wilson_rt<P, RC, NTH><<<dim3((unsigned)gx, nchunks), NTH, smem, st>>>(Ls, Lt, v.g, rmax, tmax, ntc, nrc * RC,
-                                                                         s.partials);
+                                                                         tile, s.partials);
   count_launches(1);
   const int64_t V = 2 * v.g.vh;
   k_wilson_rt_final<RC><<<rmax * tmax, kThreads, 0, st>>>(s.partials, (int)gx, ntc, tmax, 1.0 / (3.0 * (double)V),
@@ -1044,27 +1056,35 @@ static cudaError_t launch_wilson_rt_rc(const LatticeView& v, const void* spatial
   return cudaGetLastError();
 }
 
-// The time-outer plane kernel, where a plane's two link planes fit in shared
-// memory; *used = false otherwise.
+// The time-outer kernel with as many time slices per work unit as fit in
+// shared memory next to the ntc * 16 slices of line overhang (the whole
+// plane when it fits); *used = false if not even one slice fits.  FP64 runs
+// 8-wide R chunks (register budget).
 template <int P>
 static cudaError_t launch_wilson_rt(const LatticeView& v, const void* spatial, int rmax, int tmax,
                                     const Scratch& s, cudaStream_t st, bool* used) {
   using R = typename Real<P>::T;
   *used = false;
-  if constexpr (P == kF64) {
-    return cudaSuccess;  // FP64 planes take the older plane kernel (half the links per plane fit)
-  } else {
   if (!SU2_WILSON_RT) return cudaSuccess;
   const int nmax = v.g.n[0] > v.g.n[1] ? (v.g.n[0] > v.g.n[2] ? v.g.n[0] : v.g.n[2])
                                        : (v.g.n[1] > v.g.n[2] ? v.g.n[1] : v.g.n[2]);
-  const int rc = rmax <= 8 ? 8 : 16;
+  const int rc = (rmax <= 8 || P == kF64) ? 8 : 16;
   const int pad = (rmax + rc - 1) / rc * rc;  // columns a .. a + pad - 1 of a row
-  const int smem = 2 * (nmax + pad) * v.g.n[3] * (int)sizeof(Quat<R>);
-  if (smem > kWilsonRtSmemMax) return cudaSuccess;
-  *used = true;
-  if (rc == 8) return launch_wilson_rt_rc<P, 8>(v, spatial, rmax, tmax, smem, s, st);
-  return launch_wilson_rt_rc<P, 16>(v, spatial, rmax, tmax, smem, s, st);
+  const int overhang = (tmax + kWrtT - 1) / kWrtT * kWrtT;
+  const int row_bytes = 2 * (nmax + pad) * (int)sizeof(Quat<R>);
+  int tile, smem;
+  if (row_bytes * v.g.n[3] <= kWilsonRtSmemMax) {
+    tile = v.g.n[3];  // the whole plane, rows read modulo nt
+    smem = row_bytes * tile;
+  } else {
+    tile = kWilsonRtSmemMax / row_bytes - overhang;
+    if (tile < 1) return cudaSuccess;
+    smem = row_bytes * (tile + overhang);
   }
+  *used = true;
+  if (rc == 8) return launch_wilson_rt_rc<P, 8>(v, spatial, rmax, tmax, tile, smem, s, st);
+  if constexpr (P != kF64) return launch_wilson_rt_rc<P, 16>(v, spatial, rmax, tmax, tile, smem, s, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_wilson(const LatticeView& v, const void* spatial, int rmax, int tmax,

@@ -246,7 +246,11 @@ _WILSON_REF = {}
 
 @pytest.mark.parametrize("prec", ["f32", "f16q", "f64"])
 @pytest.mark.parametrize("dims,rmax,tmax", [((18, 18, 18, 4), 17, 4), ((12, 12, 12, 4), 12, 4),
-                                            ((4, 4, 4, 18), 4, 18), ((6, 10, 8, 6), 6, 6)])
+                                            ((4, 4, 4, 18), 4, 18), ((6, 10, 8, 6), 6, 6),
+                                            # 64-site rows with 96 slices: planes too large for
+                                            # shared memory, so work units are bands of time
+                                            # slices (76 / 60 slices in FP32, 30 / 14 in FP64)
+                                            ((64, 2, 2, 96), 2, 16), ((64, 2, 2, 96), 2, 20)])
 def test_wilson_loops_across_chunks(dims, rmax, tmax, prec):
     U = inputs.random_field(dims, 23)
     ref = as_stored(U, prec)
