@@ -478,158 +478,6 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson(Links<P> Ls, Links<P>
 }
 
 // ---------------------------------------------------------------------------
-// Wilson loops from shared memory.  Every loop of spatial direction MU lies
-// in the (MU, time) plane through its site, so the lattice splits into
-// independent planes (one per MU and transverse spatial position).  A block
-// stages one plane's MU links and time links in shared memory (coalesced
-// loads), then each thread takes sites of the plane and runs the same line
-// products as wilson_site, reading links from shared memory.  Blocks are
-// persistent: block b takes planes b, b + gridDim.x, ..., so each block's
-// per-(R, T) sums are a fixed function of the grid and the result is
-// reproducible.  blockIdx.y = T chunk.
-// ---------------------------------------------------------------------------
-template <int P, int TC, int NTH>
-__global__ void __launch_bounds__(NTH) k_wilson_plane(Links<P> Ls, Links<P> Lt, Geom g, int rmax, int tmax,
-                                                      double* partials) {
-  using R = typename Real<P>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double acc[kWilsonMaxR * TC];
-  const int lane = threadIdx.x & 31;
-  const int chunk = blockIdx.y;
-  const int t0 = chunk * TC;
-  const int nT = min(TC, tmax - t0);
-  const int nt = g.n[3];
-  for (int i = threadIdx.x; i < kWilsonMaxR * TC; i += NTH) acc[i] = 0.0;
-  // planes: mu in 0..2; transverse positions of the two other spatial axes
-  const int ntr0 = g.n[1] * g.n[2], ntr1 = g.n[0] * g.n[2], ntr2 = g.n[0] * g.n[1];
-  const int nplanes = ntr0 + ntr1 + ntr2;
-  for (int pl = blockIdx.x; pl < nplanes; pl += gridDim.x) {
-    const int mu = pl < ntr0 ? 0 : (pl < ntr0 + ntr1 ? 1 : 2);
-    const int tr = pl - (mu == 0 ? 0 : (mu == 1 ? ntr0 : ntr0 + ntr1));
-    const int nm = mu == 0 ? g.n[0] : (mu == 1 ? g.n[1] : g.n[2]);
-    const int np = nm * nt;
-    Quat<R>* us = reinterpret_cast<Quat<R>*>(smem_raw);   // us[a + nm t]: U_mu(a, t)
-    Quat<R>* ut = us + np;                                // ut[a + nm t]: U_t(a, t)
-    // transverse coordinates (the two spatial axes other than mu, lower first)
-    const int n1st = mu == 0 ? g.n[1] : g.n[0];  // extent of the lower transverse axis
-    const int c1 = tr % n1st, c2 = tr / n1st;
-    __syncthreads();  // the previous plane's readers are done
-    for (int i = threadIdx.x; i < np; i += NTH) {
-      const int a = i % nm, t = i / nm;
-      Site y;
-      y.x0 = mu == 0 ? a : c1;
-      y.x1 = mu == 0 ? c1 : (mu == 1 ? a : c2);
-      y.x2 = mu == 2 ? a : c2;
-      y.x3 = t;
-      y.row = y.x1 + g.n[1] * (y.x2 + g.n[2] * y.x3);
-      const int h = hidx(g, y), par = parity(y);
-      us[i] = Ls.ld(2 * mu + par, h);
-      ut[i] = Lt.ld(6 + par, h);
-    }
-    __syncthreads();
-    for (int base = 0; base < np; base += NTH) {
-      const int i = base + threadIdx.x;
-      const bool valid = i < np;
-      const int a0 = valid ? i % nm : 0, tx = valid ? i / nm : 0;
-      Quat<R> D[TC], C[TC];
-      {
-        Quat<R> pr = qone<R>();
-        int t = tx;
-        for (int k = 0; k < t0; ++k) { pr = qmul(pr, ut[a0 + nm * t]); t = t + 1 == nt ? 0 : t + 1; }
-#pragma unroll
-        for (int j = 0; j < TC; ++j) {
-          if (j < nT) { pr = qmul(pr, ut[a0 + nm * t]); t = t + 1 == nt ? 0 : t + 1; }
-          D[j] = pr;
-          C[j] = qone<R>();
-        }
-      }
-      Quat<R> A = qone<R>();
-      int ar = a0;                                  // a + r - 1
-      int tz = tx + t0 + 1; if (tz >= nt) tz -= nt;   // t + t0 + 1
-      for (int r = 1; r <= rmax; ++r) {
-        A = qmul(A, us[ar + nm * tx]);
-        {
-          int t = tz;
-#pragma unroll
-          for (int j = 0; j < TC; ++j) {
-            if (j < nT) { C[j] = qmul(C[j], us[ar + nm * t]); t = t + 1 == nt ? 0 : t + 1; }
-          }
-        }
-        ar = ar + 1 == nm ? 0 : ar + 1;
-        Quat<R> b = qone<R>();
-        int t = tx;
-        for (int k = 0; k < t0; ++k) { b = qmul(b, ut[ar + nm * t]); t = t + 1 == nt ? 0 : t + 1; }
-        R val[TC];
-#pragma unroll
-        for (int j = 0; j < TC; ++j) {
-          val[j] = R(0);
-          if (j < nT) {
-            b = qmul(b, ut[ar + nm * t]);
-            t = t + 1 == nt ? 0 : t + 1;
-            if (valid) val[j] = qdot(qmul(A, b), qmul(D[j], C[j]));
-          }
-        }
-        int nv = TC;
-        int lo = 0;
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-          if (nv > 1) {
-            const bool upper = (lane & off) != 0;
-            const int half = nv / 2;
-#pragma unroll
-            for (int k = 0; k < TC / 2; ++k) {
-              if (k < half) {
-                const R send = upper ? val[k] : val[k + half];
-                const R keep = upper ? val[k + half] : val[k];
-                val[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-              }
-            }
-            if (upper) lo += half;
-            nv = half;
-          } else {
-            val[0] += __shfl_xor_sync(0xffffffffu, val[0], off);
-          }
-        }
-        if ((lane & (32 / TC - 1)) == 0 && lo < nT) atomicAdd(&acc[(r - 1) * TC + lo], (double)val[0]);
-      }
-    }
-  }
-  __syncthreads();
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  const int per = rmax * TC;
-  for (int i = threadIdx.x; i < per; i += NTH) partials[(size_t)bid * per + i] = acc[i];
-}
-
-// out[(R-1) tmax + (T-1)] from the plane kernel's per-block sums: one block per
-// output adds the gx blocks of T's chunk in a fixed order.
-template <int TC>
-__global__ void __launch_bounds__(kThreads) k_wilson_plane_final(const double* partials, int gx, int rmax, int tmax,
-                                                                 double inv, double* out) {
-  __shared__ double ss[kThreads / 32], sc[kThreads / 32];
-  const int o = blockIdx.x;
-  const int r = o / tmax, t = o % tmax;
-  const int c = t / TC, j = t % TC;
-  const int per = rmax * TC;
-  KSum a;
-  for (int bx = threadIdx.x; bx < gx; bx += blockDim.x)
-    a.add(__ldcg(partials + (size_t)(c * gx + bx) * per + r * TC + j));
-  a = warp_ksum(a);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { ss[warp] = a.s; sc[warp] = a.c; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    KSum tot;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      KSum q;
-      q.s = ss[w];
-      q.c = sc[w];
-      tot = ksum_combine(tot, q);
-    }
-    out[o] = tot.value() * inv;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Wilson loops, time-outer form.  In the (MU, time) plane with coordinates
 // (a, t), S_R(a, t) = U_MU(a, t) ... U_MU(a+R-1, t) and T_T(a, t) = U_t(a, t)
 // ... U_t(a, t+T-1), the loop of Eq. 18 at (a, t) is
@@ -965,52 +813,6 @@ template <int P> struct WilsonChunk { static constexpr int tc = 16; };
 template <> struct WilsonChunk<kF64> { static constexpr int tc = 8; };
 
 // Plane kernel shape per arithmetic precision: T chunk and block size.
-template <int P> struct WPlane { static constexpr int tc = 8, nth = 512; };
-template <> struct WPlane<kF64> { static constexpr int tc = 4, nth = 256; };
-constexpr int kWilsonPlaneSmemMax = 200 * 1024;
-
-template <int P>
-static cudaError_t launch_wilson_plane(const LatticeView& v, const void* spatial, int rmax, int tmax,
-                                       const Scratch& s, cudaStream_t st, bool* used) {
-  using R = typename Real<P>::T;
-  constexpr int TC = WPlane<P>::tc, NTH = WPlane<P>::nth;
-  *used = false;
-  const int nmax = v.g.n[0] > v.g.n[1] ? (v.g.n[0] > v.g.n[2] ? v.g.n[0] : v.g.n[2])
-                                       : (v.g.n[1] > v.g.n[2] ? v.g.n[1] : v.g.n[2]);
-  const int smem = 2 * nmax * v.g.n[3] * (int)sizeof(Quat<R>);
-  if (smem > kWilsonPlaneSmemMax) return cudaSuccess;
-  static bool attr_set[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_wilson_plane<P, TC, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kWilsonPlaneSmemMax);
-    if (e != cudaSuccess) return e;
-    attr_set[dev] = true;
-  }
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson_plane<P, TC, NTH>, NTH, smem);
-  if (per_sm < 1) per_sm = 1;
-  const int nchunks = (tmax + TC - 1) / TC;
-  const int nplanes = v.g.n[1] * v.g.n[2] + v.g.n[0] * v.g.n[2] + v.g.n[0] * v.g.n[1];
-  int64_t gx = (int64_t)device_info().sms * per_sm / nchunks;
-  if (gx > nplanes) gx = nplanes;
-  const int64_t per = (int64_t)rmax * TC;
-  const int64_t cap = (int64_t)kScratchPartials / per / nchunks;
-  if (gx > cap) gx = cap;
-  if (gx < 1) gx = 1;
-  auto Lt = links_of<P>(v.links, v.g.vh);
-  auto Ls = links_of<P>(const_cast<void*>(spatial), v.g.vh);
-  k_wilson_plane<P, TC, NTH><<<dim3((unsigned)gx, nchunks), NTH, smem, st>>>(Ls, Lt, v.g, rmax, tmax, s.partials);
-  count_launches(1);
-  const int64_t V = 2 * v.g.vh;
-  k_wilson_plane_final<TC><<<rmax * tmax, kThreads, 0, st>>>(s.partials, (int)gx, rmax, tmax,
-                                                              1.0 / (3.0 * (double)V), s.out);
-  count_launches(1);
-  *used = true;
-  return cudaGetLastError();
-}
-
 #ifndef SU2_WILSON_RT
 #define SU2_WILSON_RT 1
 #endif
@@ -1096,13 +898,7 @@ cudaError_t launch_wilson(const LatticeView& v, const void* spatial, int rmax, i
     SU2_DISPATCH(v.prec, { e = launch_wilson_rt<P>(v, spatial, rmax, tmax, s, st, &used); });
     if (e != cudaSuccess || used) return e;
   }
-  {
-    bool used = false;
-    cudaError_t e = cudaSuccess;
-    SU2_DISPATCH(v.prec, { e = launch_wilson_plane<P>(v, spatial, rmax, tmax, s, st, &used); });
-    if (e != cudaSuccess || used) return e;
-  }
-  // planes too large for shared memory: global-memory kernel
+  // rows too long for even one time slice in shared memory: global-memory kernel
   SU2_DISPATCH(v.prec, {
     constexpr int TC = WilsonChunk<P>::tc;
     auto Lt = links_of<P>(v.links, v.g.vh);

@@ -250,7 +250,10 @@ _WILSON_REF = {}
                                             # 64-site rows with 96 slices: planes too large for
                                             # shared memory, so work units are bands of time
                                             # slices (76 / 60 slices in FP32, 30 / 14 in FP64)
-                                            ((64, 2, 2, 96), 2, 16), ((64, 2, 2, 96), 2, 20)])
+                                            ((64, 2, 2, 96), 2, 16), ((64, 2, 2, 96), 2, 20),
+                                            # 432-site rows: not even one time slice (plus the
+                                            # lines' overhang) fits, the global-memory kernel runs
+                                            ((432, 2, 2, 16), 2, 16)])
 def test_wilson_loops_across_chunks(dims, rmax, tmax, prec):
     U = inputs.random_field(dims, 23)
     ref = as_stored(U, prec)
