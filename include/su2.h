@@ -247,9 +247,9 @@ int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smeared, double
  * Copy links to / from caller-owned host memory in the canonical FP64 layout
  * (4V quaternions, 16 doubles per site).  set_links converts to the handle's
  * precision (F16Q rounds to binary16), invalidates the smeared copy and keeps
- * the sweep counter.  Both synchronise.  With page-locked host memory
- * (cudaHostAlloc, cudaHostRegister) the conversion kernel reads or writes
- * the host buffer directly; pageable memory goes through a device staging
+ * the sweep counter.  Both synchronise.  set_links from page-locked host
+ * memory (cudaHostAlloc, cudaHostRegister) lets the conversion kernel read
+ * the host buffer directly; everything else goes through a device staging
  * buffer in chunks.
  */
 int su2_get_links(su2_lattice* h, double* host);

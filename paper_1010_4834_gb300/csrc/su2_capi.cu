@@ -563,8 +563,8 @@ extern "C" int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smea
 }
 
 // The device-visible address of page-locked host memory (cudaHostAlloc,
-// cudaHostRegister: the conversion kernels then read or write it directly
-// over the host link), or NULL for pageable memory.
+// cudaHostRegister: the conversion kernel then reads it directly over the
+// host link, at the copy engine's rate), or NULL for pageable memory.
 static void* host_mapped(const void* host) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
@@ -574,14 +574,11 @@ static void* host_mapped(const void* host) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
-// Sites [first, first + count) in canonical FP64 order into host[16 * count].
+// Sites [first, first + count) in canonical FP64 order into host[16 * count],
+// through the device staging buffer and the copy engine (kernel stores to
+// host memory run at a fraction of the copy engine's rate over the host link).
 static int copy_sites_out(su2_lattice* h, int64_t first, int64_t count, double* host) {
   DeviceGuard dg(h->device);
-  if (void* d = count > 0 ? host_mapped(host) : nullptr) {
-    SU2_CU(launch_to_canonical(view(h), static_cast<double*>(d), first, count, h->stream));
-    SU2_CU(cudaStreamSynchronize(h->stream));
-    return SU2_OK;
-  }
   for (int64_t k = 0; k < count; k += h->staging_sites) {
     const int64_t ns = count - k < h->staging_sites ? count - k : h->staging_sites;
     SU2_CU(launch_to_canonical(view(h), h->staging, first + k, ns, h->stream));

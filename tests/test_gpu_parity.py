@@ -86,9 +86,9 @@ def test_set_get_roundtrip(prec):
 
 @pytest.mark.parametrize("prec", ["f64", "f16q"])
 def test_pinned_host_buffers_take_the_direct_path(prec):
-    # page-locked buffers are read and written by the conversion kernels
-    # directly; the result must equal the staged copy of pageable memory,
-    # also for a site range in the middle of the buffer
+    # a page-locked source is read by the conversion kernel directly; the
+    # result must equal the staged copy of pageable memory, and reading back
+    # into page-locked buffers (whole and a site range) must agree too
     import torch
     dims = (8, 6, 4, 10)
     U = inputs.random_field(dims, 17)
