@@ -137,6 +137,59 @@ def step(lat, hist):
     return lat.wilson_loops(RMAX, TMAX, smeared=True)
 
 
+def small_configs(torch):
+    """The other configurations the benchmark's lattice is quoted beside, each
+    run once as specified (their own sweep counts and measurements) and
+    reported as link updates/s over the device time of the whole run."""
+    import numpy as np
+    from paper_1010_4834_gb300 import Lattice
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    out = {}
+    # 8^4, beta 2.4, cold, FP64: 100 sweeps, plaquette and Polyakov after each
+    lat = Lattice((8, 8, 8, 8), 2.4, seed=1, start="cold", prec="f64")
+    t = timed(lambda: lat.sweep_measure(100))
+    out["8^4_f64_cold_100sweeps_measured"] = 100 * 4 * 8 ** 4 / t
+    lat.close()
+    # 16^4, beta 2.5, hot, FP32: 500 sweeps, then 25 APE steps and W(R,T <= 8)
+    lat = Lattice((16, 16, 16, 16), 2.5, seed=1, start="hot", prec="f32")
+
+    def c2():
+        lat.sweep(500)
+        lat.ape_smear(0.7, 25)
+        lat.wilson_loops(8, 8, smeared=True)
+    t = timed(c2)
+    out["16^4_f32_hot_500sweeps_ape25_W8x8"] = 500 * 4 * 16 ** 4 / t
+    lat.close()
+    # 32^3 x 4 at 16 betas in [2.2, 2.6]: 1000 measured sweeps each, FP32 and
+    # F16Q; one lattice is too small to fill the GPU, so the 16 chains run
+    # concurrently, each on its own stream driven by its own host thread
+    from concurrent.futures import ThreadPoolExecutor
+    for prec in ("f32", "f16q"):
+        lats = [Lattice((32, 32, 32, 4), float(b), seed=1 + i, start="hot", prec=prec, stream=torch.cuda.Stream())
+                for i, b in enumerate(np.linspace(2.2, 2.6, 16))]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(len(lats)) as ex:
+            list(ex.map(lambda x: x.sweep_measure(1000), lats))
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out["32^3x4_%s_16betas_1000sweeps_measured" % prec] = 16 * 1000 * 4 * 32 ** 3 * 4 / t
+        for x in lats:
+            x.close()
+    return {"unit": UNIT, "values": out,
+            "what": "each configuration's whole run (sweeps and its measurements): device time, and for the "
+                    "32^3x4 scan the wall time of its 16 chains run concurrently on 16 streams"}
+
+
 def timed_sweeps(torch, lat, n, reps=3):
     """Device time of n heat-bath sweeps (graph path), best of reps."""
     best = None
@@ -374,6 +427,7 @@ def run_gpu_on_stream(args):
             extra[prec] = {"value": n * 4 * V / timed_sweeps(torch, l2, n, reps=2), "unit": UNIT,
                            "what": "%s 64^4 heat-bath sweeps alone, %d sweeps" % (prec, n)}
             l2.close()
+        extra["configs"] = small_configs(torch)
         betas = inputs.batch_betas(len(BATCH_SHAPES), seed=1)
         b = Batch(BATCH_SHAPES, betas, seed=1, start="hot", prec="f32")
         groups = b.tune(4)
