@@ -556,31 +556,11 @@ template <int D, int S> __device__ __forceinline__ int half_step(const Geom& g, 
 // The two staple terms of Section 2 Eq. 11 for link (x, MU) and one NU != MU:
 // U_nu(x) U_mu(x+nu) U_nu(x+mu)^dagger + U_nu(x-nu)^dagger U_mu(x-nu)
 // U_nu(x-nu+mu).  U_nu(x) and U_nu(x-nu+mu) have the parity p of x; the four
-// singly shifted links have parity 1-p.
+// singly shifted links have parity 1-p.  Neighbour indices come from
+// half-index steps (dmu = the step x -> x + MU).
 template <int P, int MU, int NU, bool NC, bool CP>
-__device__ __forceinline__ void staple_term(const Links<P, CP>& L, const Geom& g, const Site& x, int h,
-                                            int h_pmu, int p, Quat<typename Real<P>::T>& s) {
-  using R = typename Real<P>::T;
-  const int q = p ^ 1;
-  const Site xmnu = shifted<NU, -1>(g, x);
-  const int h_pnu = hidx(g, shifted<NU, +1>(g, x));
-  const int h_mnu = hidx(g, xmnu);
-  const int h_mp = hidx(g, shifted<MU, +1>(g, xmnu));
-  const Quat<R> a = ldl<P, NC>(L, 2 * NU + p, h);       // U_nu(x)
-  const Quat<R> b = ldl<P, NC>(L, 2 * MU + q, h_pnu);   // U_mu(x+nu)
-  const Quat<R> c = ldl<P, NC>(L, 2 * NU + q, h_pmu);   // U_nu(x+mu)
-  const Quat<R> d = ldl<P, NC>(L, 2 * NU + q, h_mnu);   // U_nu(x-nu)
-  const Quat<R> e = ldl<P, NC>(L, 2 * MU + q, h_mnu);   // U_mu(x-nu)
-  const Quat<R> f = ldl<P, NC>(L, 2 * NU + p, h_mp);    // U_nu(x-nu+mu)
-  qacc_mul_nd(s, qmul(a, b), c);
-  qacc_mul(s, qmul_dn(d, e), f);
-}
-
-// staple_term with the neighbour indices from half-index steps (dmu = the
-// step x -> x + MU): the same loads and products in the same order.
-template <int P, int MU, int NU, bool NC, bool CP>
-__device__ __forceinline__ void staple_term_steps(const Links<P, CP>& L, const Geom& g, const Site& x, int h, int dmu,
-                                                  int p, Quat<typename Real<P>::T>& s) {
+__device__ __forceinline__ void staple_term(const Links<P, CP>& L, const Geom& g, const Site& x, int h, int dmu,
+                                            int p, Quat<typename Real<P>::T>& s) {
   using R = typename Real<P>::T;
   const int q = p ^ 1;
   const int h_mnu = h + half_step<NU, -1>(g, x);
@@ -594,73 +574,18 @@ __device__ __forceinline__ void staple_term_steps(const Links<P, CP>& L, const G
   qacc_mul(s, qmul_dn(d, e), f);
 }
 
-// The six links of staple_term, loaded (no arithmetic).
-template <class R> struct StapleLinks { Quat<R> a, b, c, d, e, f; };
-
-template <int P, int MU, int NU, bool NC, bool CP>
-__device__ __forceinline__ void staple_load(const Links<P, CP>& L, const Geom& g, const Site& x, int h, int h_pmu,
-                                            int p, StapleLinks<typename Real<P>::T>& t) {
-  const int q = p ^ 1;
-  const Site xmnu = shifted<NU, -1>(g, x);
-  const int h_pnu = hidx(g, shifted<NU, +1>(g, x));
-  const int h_mnu = hidx(g, xmnu);
-  const int h_mp = hidx(g, shifted<MU, +1>(g, xmnu));
-  t.a = ldl<P, NC>(L, 2 * NU + p, h);
-  t.b = ldl<P, NC>(L, 2 * MU + q, h_pnu);
-  t.c = ldl<P, NC>(L, 2 * NU + q, h_pmu);
-  t.d = ldl<P, NC>(L, 2 * NU + q, h_mnu);
-  t.e = ldl<P, NC>(L, 2 * MU + q, h_mnu);
-  t.f = ldl<P, NC>(L, 2 * NU + p, h_mp);
-}
-
-template <class R> __device__ __forceinline__ void staple_add(const StapleLinks<R>& t, Quat<R>& s) {
-  qacc_mul_nd(s, qmul(t.a, t.b), t.c);
-  qacc_mul(s, qmul_dn(t.d, t.e), t.f);
-}
-
-#ifndef SU2_STAPLE_LOADS_FIRST
-#define SU2_STAPLE_LOADS_FIRST 0
-#endif
-#ifndef SU2_STAPLE_STEPS
-#define SU2_STAPLE_STEPS 1
-#endif
-
 // Staple sum for link (x, MU) over the directions NU != MU selected by NMASK
-// (0xF: all, the heat bath; 0x7: the spatial ones, APE smearing).  With
-// SU2_STAPLE_LOADS_FIRST the loads of all directions are issued before any
-// product, so a warp has every load of the update in flight at once.
+// (0xF: all, the heat bath), NU ascending.
 template <int P, int MU, int NMASK, bool NC, bool CP>
 __device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P, CP>& L, const Geom& g,
                                                            const Site& x, int h, int p) {
   using R = typename Real<P>::T;
   Quat<R> s = qmake<R>(0, 0, 0, 0);
-  const int h_pmu = hidx(g, shifted<MU, +1>(g, x));
-  if (SU2_STAPLE_LOADS_FIRST) {
-    // the three directions NU != MU (for NMASK 0x7 and MU < 3 only two)
-    constexpr int N0 = MU == 0 ? 1 : 0;
-    constexpr int N1 = MU <= 1 ? 2 : 1;
-    constexpr int N2 = MU <= 2 ? 3 : 2;
-    StapleLinks<R> t0, t1, t2;
-    if (NMASK & (1 << N0)) staple_load<P, MU, N0, NC>(L, g, x, h, h_pmu, p, t0);
-    if (NMASK & (1 << N1)) staple_load<P, MU, N1, NC>(L, g, x, h, h_pmu, p, t1);
-    if (NMASK & (1 << N2)) staple_load<P, MU, N2, NC>(L, g, x, h, h_pmu, p, t2);
-    if (NMASK & (1 << N0)) staple_add(t0, s);
-    if (NMASK & (1 << N1)) staple_add(t1, s);
-    if (NMASK & (1 << N2)) staple_add(t2, s);
-    return s;
-  }
-  if (SU2_STAPLE_STEPS) {
-    const int dmu = half_step<MU, +1>(g, x);
-    if (MU != 0 && (NMASK & 1)) staple_term_steps<P, MU, 0, NC>(L, g, x, h, dmu, p, s);
-    if (MU != 1 && (NMASK & 2)) staple_term_steps<P, MU, 1, NC>(L, g, x, h, dmu, p, s);
-    if (MU != 2 && (NMASK & 4)) staple_term_steps<P, MU, 2, NC>(L, g, x, h, dmu, p, s);
-    if (MU != 3 && (NMASK & 8)) staple_term_steps<P, MU, 3, NC>(L, g, x, h, dmu, p, s);
-    return s;
-  }
-  if (MU != 0 && (NMASK & 1)) staple_term<P, MU, 0, NC>(L, g, x, h, h_pmu, p, s);
-  if (MU != 1 && (NMASK & 2)) staple_term<P, MU, 1, NC>(L, g, x, h, h_pmu, p, s);
-  if (MU != 2 && (NMASK & 4)) staple_term<P, MU, 2, NC>(L, g, x, h, h_pmu, p, s);
-  if (MU != 3 && (NMASK & 8)) staple_term<P, MU, 3, NC>(L, g, x, h, h_pmu, p, s);
+  const int dmu = half_step<MU, +1>(g, x);
+  if (MU != 0 && (NMASK & 1)) staple_term<P, MU, 0, NC>(L, g, x, h, dmu, p, s);
+  if (MU != 1 && (NMASK & 2)) staple_term<P, MU, 1, NC>(L, g, x, h, dmu, p, s);
+  if (MU != 2 && (NMASK & 4)) staple_term<P, MU, 2, NC>(L, g, x, h, dmu, p, s);
+  if (MU != 3 && (NMASK & 8)) staple_term<P, MU, 3, NC>(L, g, x, h, dmu, p, s);
   return s;
 }
 
@@ -673,42 +598,16 @@ __device__ __forceinline__ Quat<typename Real<P>::T> staple_split(const Links<P,
                                                                  int h, int p, Quat<typename Real<P>::T>& lower) {
   using R = typename Real<P>::T;
   Quat<R> s = qmake<R>(0, 0, 0, 0);
-  if (SU2_STAPLE_STEPS) {
-    const int dmu = half_step<MU, +1>(g, x);
-    if (MU != 0) staple_term_steps<P, MU, 0, NC>(L, g, x, h, dmu, p, s);
-    if (MU == 1) lower = s;
-    if (MU != 1) staple_term_steps<P, MU, 1, NC>(L, g, x, h, dmu, p, s);
-    if (MU == 2) lower = s;
-    if (MU != 2) staple_term_steps<P, MU, 2, NC>(L, g, x, h, dmu, p, s);
-    if (MU == 3) lower = s;
-    if (MU != 3) staple_term_steps<P, MU, 3, NC>(L, g, x, h, dmu, p, s);
-  } else {
-    const int h_pmu = hidx(g, shifted<MU, +1>(g, x));
-    if (MU != 0) staple_term<P, MU, 0, NC>(L, g, x, h, h_pmu, p, s);
-    if (MU == 1) lower = s;
-    if (MU != 1) staple_term<P, MU, 1, NC>(L, g, x, h, h_pmu, p, s);
-    if (MU == 2) lower = s;
-    if (MU != 2) staple_term<P, MU, 2, NC>(L, g, x, h, h_pmu, p, s);
-    if (MU == 3) lower = s;
-    if (MU != 3) staple_term<P, MU, 3, NC>(L, g, x, h, h_pmu, p, s);
-  }
+  const int dmu = half_step<MU, +1>(g, x);
+  if (MU != 0) staple_term<P, MU, 0, NC>(L, g, x, h, dmu, p, s);
+  if (MU == 1) lower = s;
+  if (MU != 1) staple_term<P, MU, 1, NC>(L, g, x, h, dmu, p, s);
+  if (MU == 2) lower = s;
+  if (MU != 2) staple_term<P, MU, 2, NC>(L, g, x, h, dmu, p, s);
+  if (MU == 3) lower = s;
+  if (MU != 3) staple_term<P, MU, 3, NC>(L, g, x, h, dmu, p, s);
   if (MU == 0) lower = qmake<R>(0, 0, 0, 0);
   return s;
-}
-
-// One heat-bath update of link (x, MU): staple, draw, store (a capped link
-// is neither read nor written).  Returns the draw's trial count.
-template <int P, int MU, bool NC, bool CP>
-__device__ __forceinline__ int heatbath_site(const Links<P, CP>& L, const Geom& g, const Site& x, int h,
-                                             int p, uint32_t sweep, const HBParams& hp,
-                                             typename Real<P>::T beta) {
-  using R = typename Real<P>::T;
-  const Quat<R> sig = staple<P, MU, 0xF, NC>(L, g, x, h, p);
-  Quat<R> nl;
-  const uint4 ctr = make_uint4(site_index(g, x), (uint32_t)MU | hp.lattice_tag, sweep, 0u);
-  const int n = heatbath_draw<R>(sig, ctr, hp, beta, &nl);
-  if (n != 0) L.st(2 * MU + p, h, nl);
-  return n;
 }
 
 }  // namespace su2
