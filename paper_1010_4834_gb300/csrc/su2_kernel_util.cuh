@@ -11,12 +11,12 @@ constexpr int kThreads = 256;
 // Blocks for `work` items with a grid-stride loop: every SM filled to the
 // kernel's occupancy, never more blocks than items need.
 template <class K>
-static int grid_for(K kernel, int64_t work, int smem = 0) {
+static int grid_for(K kernel, int64_t work, int smem = 0, int block = kThreads) {
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
   if (per_sm < 1) per_sm = 1;
   const int64_t full = (int64_t)device_info().sms * per_sm;
-  const int64_t need = (work + kThreads - 1) / kThreads;
+  const int64_t need = (work + block - 1) / block;
   int64_t g = need < full ? need : full;
   return (int)(g < 1 ? 1 : g);
 }
