@@ -15,7 +15,7 @@ namespace su2 {
 // loop until its slowest lane accepts.  So every lane makes trial 1 inline;
 // a link that rejects it goes to a block-wide shared-memory queue (its
 // W = Sigma/k, alpha, index and site), which the whole block drains every
-// kDeferEvery iterations with trials 2, 3, ...  The draws and their order are
+// DeferEvery iterations with trials 2, 3, ...  The draws and their order are
 // those of the plain loop, so results are identical; only the schedule
 // differs.  A full queue falls back to finishing the link inline.
 //
@@ -45,7 +45,11 @@ template <> struct HbBlock<kF64> { static constexpr int value = 256; };
 template <int P, bool MEAS> struct DeferCap {
   static constexpr int value = MEAS ? 2 * HbBlock<P>::value : 4 * HbBlock<P>::value;
 };
-constexpr int kDeferEvery = 32;
+// Drain interval in block iterations: at the ~5% first-trial rejection of
+// beta ~ 2.5 a queue collects about 0.05 * 1024 * interval links, which the
+// capacity covers (the plaquette-summing variant's smaller queue, half as
+// often); fewer drains mean fewer block-wide barriers.
+template <bool MEAS> struct DeferEvery { static constexpr int value = MEAS ? 32 : 64; };
 
 template <class R> struct PlainAcc {
   R s = R(0);
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(HbBlock<P>::value, Occ<P>::hb * kThreads / HbB
         }
       }
     }
-    if ((it % kDeferEvery) == kDeferEvery - 1 || base + stride >= vh) {
+    if ((it % DeferEvery<MEAS>::value) == DeferEvery<MEAS>::value - 1 || base + stride >= vh) {
       __syncthreads();
       const int n = min(qn, kDeferCap);
       for (int i = threadIdx.x; i < n; i += blockDim.x) {

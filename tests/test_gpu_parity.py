@@ -554,8 +554,8 @@ def test_sweep_plaquette_matches_plaquette_kernel(prec, tol, beta, max_tries, sa
 @pytest.mark.parametrize("n,beta", [(32, 2.5), (48, 0.05)])
 def test_sweep_plaquette_full_size_grid(n, beta):
     # the substeps run the full persistent grid, several iterations per block;
-    # at beta 0.05 on 48^4 (17 iterations of 256 links per block) most first
-    # trials fail, the block queues overflow (1024 entries) and some links
+    # at beta 0.05 on 48^4 (17 iterations of 1024 links per block) most first
+    # trials fail, the block queues overflow (4096 entries) and some links
     # exhaust their trials
     a = Lattice((n,) * 4, beta, seed=43, start="hot", prec="f32")
     b = Lattice((n,) * 4, beta, seed=43, start="hot", prec="f32")
