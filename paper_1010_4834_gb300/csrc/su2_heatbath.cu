@@ -34,17 +34,17 @@ namespace su2 {
 // Queue capacity: the plaquette-summing variant's entries are larger (they
 // carry the partial staple), so it keeps fewer and leaves the SM's L1 share
 // of the shared-memory carveout about the same.
-// Block size: large blocks share one deferral queue among more threads and
-// drain it less often per link (64^4 FP32 substep: 203 us at 256 threads,
-// 201 at 512, 196 at 1024).  FP64 needs 128 registers a thread, so 256.
-#ifndef SU2_HB_THREADS
-#define SU2_HB_THREADS 1024
+// Block size BS: on large lattices blocks of 1024 share one deferral queue
+// among more threads, which drain it less often per link (FP32 substep on
+// 64^4, 55 k half-sites per SM: 202 us at 256 threads, 194 at 1024); up to
+// 48^4 (17 k per SM) 256 is faster (70.9 against 72.2 us; 16^4 12.3
+// against 14.0), as more, smaller blocks spread the few block iterations
+// evenly over the SMs.  The switch is at SU2_HB_BIG_PER_SM half-lattice
+// sites per SM.  FP64 needs 128 registers a thread, so 256 always.
+#ifndef SU2_HB_BIG_PER_SM
+#define SU2_HB_BIG_PER_SM 32768
 #endif
-template <int P> struct HbBlock { static constexpr int value = SU2_HB_THREADS; };
-template <> struct HbBlock<kF64> { static constexpr int value = 256; };
-template <int P, bool MEAS> struct DeferCap {
-  static constexpr int value = MEAS ? 2 * HbBlock<P>::value : 4 * HbBlock<P>::value;
-};
+template <int BS, bool MEAS> struct DeferCap { static constexpr int value = MEAS ? 2 * BS : 4 * BS; };
 // Drain interval in block iterations: at the ~5% first-trial rejection of
 // beta ~ 2.5 a queue collects about 0.05 * 1024 * interval links, which the
 // capacity covers (the plaquette-summing variant's smaller queue, half as
@@ -80,16 +80,16 @@ __device__ __forceinline__ int finish_deferred(const Deferred<R, MEAS>& d, uint4
   return n;
 }
 
-template <int P, int MU, bool MEAS, int PAR>
-__global__ void __launch_bounds__(HbBlock<P>::value, Occ<P>::hb * kThreads / HbBlock<P>::value)
+template <int P, int MU, bool MEAS, int PAR, int BS>
+__global__ void __launch_bounds__(BS, Occ<P>::hb * kThreads / BS)
     k_heatbath(Links<P, true> L, Geom g, const uint32_t* sweep_base, uint32_t sweep_off,
                const __grid_constant__ HBParams hp, unsigned long long* stats, double* meas) {
   constexpr int p = PAR;
   using R = typename Real<P>::T;
   using M = Math<R>;
   using Def = Deferred<R, MEAS>;
-  constexpr int kDeferCap = DeferCap<P, MEAS>::value;
-  constexpr int kHbThreads = HbBlock<P>::value;
+  constexpr int kDeferCap = DeferCap<BS, MEAS>::value;
+  constexpr int kHbThreads = BS;
   __shared__ Def queue[kDeferCap];
   __shared__ int qn;
   const R beta = (R)hp.beta;
@@ -252,21 +252,30 @@ cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint
     // direction and parity are template parameters, so every class index in
     // the kernel is a compile-time constant: per-class base pointers
     auto L = links_of<P, true>(v.links, v.g.vh);
-    constexpr int kHbThreads = HbBlock<P>::value;
-    if (meas) {
-      if constexpr (MU >= 1) {
-        const int gr = grid_for(k_heatbath<P, MU, true, 1>, v.g.vh, 0, kHbThreads);
+    const bool big = P != kF64 && v.g.vh >= (int64_t)SU2_HB_BIG_PER_SM * device_info().sms;
+    auto launch = [&](auto kernel, int bs, double* m) -> cudaError_t {
+      const int gr = grid_for(kernel, v.g.vh, 0, bs);
+      if (m) {
         if (gr > kMeasStride) return cudaErrorInvalidConfiguration;
         *meas_blocks = gr;
-        k_heatbath<P, MU, true, 1><<<gr, kHbThreads, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, stats, meas);
+      }
+      kernel<<<gr, bs, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, stats, m);
+      return cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    if (meas) {
+      if constexpr (MU >= 1) {
+        e = big ? launch(k_heatbath<P, MU, true, 1, (P == kF64 ? 256 : 1024)>, P == kF64 ? 256 : 1024, meas)
+                : launch(k_heatbath<P, MU, true, 1, 256>, 256, meas);
       }
     } else if (parity == 0) {
-      const int gr = grid_for(k_heatbath<P, MU, false, 0>, v.g.vh, 0, kHbThreads);
-      k_heatbath<P, MU, false, 0><<<gr, kHbThreads, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, stats, nullptr);
+      e = big ? launch(k_heatbath<P, MU, false, 0, (P == kF64 ? 256 : 1024)>, P == kF64 ? 256 : 1024, nullptr)
+              : launch(k_heatbath<P, MU, false, 0, 256>, 256, nullptr);
     } else {
-      const int gr = grid_for(k_heatbath<P, MU, false, 1>, v.g.vh, 0, kHbThreads);
-      k_heatbath<P, MU, false, 1><<<gr, kHbThreads, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, stats, nullptr);
+      e = big ? launch(k_heatbath<P, MU, false, 1, (P == kF64 ? 256 : 1024)>, P == kF64 ? 256 : 1024, nullptr)
+              : launch(k_heatbath<P, MU, false, 1, 256>, 256, nullptr);
     }
+    if (e != cudaSuccess) return e;
   }));
   count_launches(1);
   return cudaGetLastError();
