@@ -63,8 +63,10 @@ struct su2_lattice {
   cudaStream_t stream;
   bool own_stream;
   cudaStream_t cap_stream;
-  cudaGraphExec_t graph;
+  cudaGraphExec_t graph;   // kGraphSweeps plain sweeps
+  cudaGraphExec_t mgraph;  // kGraphSweeps measured sweeps
   int graph_sweeps;
+  int meas_nb[3];          // blocks of the three plaquette-summing substeps
   int smeared;  // 0 none, 1 in ape[0], 2 in ape[1]
 };
 
@@ -73,7 +75,7 @@ namespace {
 constexpr int kGraphSweeps = 8;
 constexpr int64_t kStagingSites = (int64_t)1 << 18;
 
-constexpr int kHistSweeps = 1024;
+constexpr int kHistSweeps = kHistRing;
 
 struct Layout {
   size_t links, ape0, ape1, partials, counter, out, state, hist, staging, total;
@@ -150,7 +152,9 @@ static HBParams hb_params(const su2_lattice* h) {
 
 static void drop_graph(su2_lattice* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->mgraph) cudaGraphExecDestroy(h->mgraph);
   h->graph = nullptr;
+  h->mgraph = nullptr;
   h->graph_sweeps = 0;
 }
 
@@ -306,23 +310,48 @@ static cudaError_t enqueue_sweep(su2_lattice* h, uint32_t off, cudaStream_t st) 
   return cudaSuccess;
 }
 
-static int build_graph(su2_lattice* h) {
-  drop_graph(h);
+// One measured sweep: the eight substeps, the odd-parity ones of mu = 1, 2, 3
+// also summing the plaquettes their links close (see k_heatbath), then the
+// Polyakov kernel, whose last block turns those block sums into the
+// plaquette, records both in row (*d_sweep mod kHistRing) of d_hist and
+// advances *d_sweep.  No host state changes, so it replays in a graph.
+static cudaError_t enqueue_measured_sweep(su2_lattice* h, cudaStream_t st) {
+  const LatticeView v = view(h);
+  const HBParams hp = hb_params(h);
+  for (int mu = 0; mu < 4; ++mu)
+    for (int p = 0; p < 2; ++p) {
+      double* meas = (mu >= 1 && p == 1) ? h->scratch.partials + (size_t)(mu - 1) * kMeasStride : nullptr;
+      cudaError_t e = launch_heatbath(v, mu, p, h->d_sweep, 0u, hp, nullptr, st, meas, meas ? &h->meas_nb[mu - 1] : nullptr);
+      if (e != cudaSuccess) return e;
+    }
+  SweepEpilogue ep{h->scratch.partials, {h->meas_nb[0], h->meas_nb[1], h->meas_nb[2]}, (double)(2 * v.g.vh),
+                   h->d_hist, h->d_sweep};
+  Scratch sp = h->scratch;
+  sp.partials = h->scratch.partials + 3 * (size_t)kMeasStride;  // clear of the block sums
+  return launch_polyakov(v, sp, st, &ep);
+}
+
+// Capture kGraphSweeps plain (measured = false) or measured sweeps.
+static int build_graph(su2_lattice* h, bool measured) {
+  cudaGraphExec_t& exec = measured ? h->mgraph : h->graph;
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
   cudaGraph_t graph;
   CaptureScope no_count;
   SU2_CU(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < kGraphSweeps && e == cudaSuccess; ++i) e = enqueue_sweep(h, (uint32_t)i, h->cap_stream);
-  if (e == cudaSuccess) e = launch_add_u32(h->d_sweep, kGraphSweeps, h->cap_stream);
+  for (int i = 0; i < kGraphSweeps && e == cudaSuccess; ++i)
+    e = measured ? enqueue_measured_sweep(h, h->cap_stream) : enqueue_sweep(h, (uint32_t)i, h->cap_stream);
+  if (e == cudaSuccess && !measured) e = launch_add_u32(h->d_sweep, kGraphSweeps, h->cap_stream);
   cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (e2 == cudaSuccess) cudaGraphDestroy(graph);
     return fail(SU2_ECUDA, "sweep graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
-  e = cudaGraphInstantiate(&h->graph, graph, 0);
+  e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    h->graph = nullptr;
+    exec = nullptr;
     return fail(SU2_ECUDA, "sweep graph instantiation failed: %s", cudaGetErrorString(e));
   }
   h->graph_sweeps = kGraphSweeps;
@@ -339,7 +368,7 @@ extern "C" int su2_heatbath_sweep(su2_lattice* h, int n) {
   int left = n;
   if (left >= kGraphSweeps) {
     if (!h->graph) {
-      int rc = build_graph(h);
+      int rc = build_graph(h, false);
       if (rc) return rc;
     }
     while (left >= kGraphSweeps) {
@@ -374,28 +403,30 @@ extern "C" int su2_sweep_measure(su2_lattice* h, int n, double* hist) {
   if (n > 0 && !hist) return fail(SU2_EINVAL, "hist is NULL");
   if (h->sweep + (uint64_t)n >= 0xFFFFFFFFull) return fail(SU2_EINVAL, "sweep counter would reach the reserved index 2^32 - 1");
   DeviceGuard dg(h->device);
-  const LatticeView v = view(h);
   for (int c0 = 0; c0 < n; c0 += kHistSweeps) {
     const int m = n - c0 < kHistSweeps ? n - c0 : kHistSweeps;
-    for (int i = 0; i < m; ++i) {
-      // the sweep's odd-parity substeps of mu = 1, 2, 3 also sum the
-      // plaquettes their links close (see k_heatbath), so the plaquette after
-      // the sweep needs no separate pass over the links
-      const HBParams hp = hb_params(h);
-      int nb[3] = {0, 0, 0};
-      for (int mu = 0; mu < 4; ++mu)
-        for (int p = 0; p < 2; ++p) {
-          double* meas = (mu >= 1 && p == 1) ? h->scratch.partials + (size_t)(mu - 1) * kMeasStride : nullptr;
-          SU2_CU(launch_heatbath(v, mu, p, h->d_sweep, 0u, hp, nullptr, h->stream, meas, meas ? &nb[mu - 1] : nullptr));
-        }
-      SU2_CU(launch_add_u32(h->d_sweep, 1u, h->stream));
-      SU2_CU(launch_plaquette_from_sweep(h->scratch.partials, nb, 2 * v.g.vh, h->d_hist + 4 * i, h->stream));
-      Scratch sp = h->scratch;
-      sp.out = h->d_hist + 4 * i + 3;
-      SU2_CU(launch_polyakov(v, sp, h->stream));
+    int left = m;
+    if (left >= kGraphSweeps) {
+      if (!h->mgraph) {
+        int rc = build_graph(h, true);
+        if (rc) return rc;
+      }
+      while (left >= kGraphSweeps) {
+        SU2_CU(cudaGraphLaunch(h->mgraph, h->stream));
+        count_launches(9 * kGraphSweeps);
+        left -= kGraphSweeps;
+      }
     }
-    SU2_CU(cudaMemcpyAsync(hist + 4 * (size_t)c0, h->d_hist, (size_t)m * 4 * sizeof(double),
+    for (; left > 0; --left) SU2_CU(enqueue_measured_sweep(h, h->stream));
+    // sweep h->sweep + c0 + i sits in ring row (h->sweep + c0 + i) mod
+    // kHistRing: at most two contiguous pieces
+    const int r0 = (int)((h->sweep + (uint64_t)c0) % (uint64_t)kHistRing);
+    const int first = m < kHistRing - r0 ? m : kHistRing - r0;
+    SU2_CU(cudaMemcpyAsync(hist + 4 * (size_t)c0, h->d_hist + 4 * (size_t)r0, (size_t)first * 4 * sizeof(double),
                            cudaMemcpyDeviceToHost, h->stream));
+    if (m > first)
+      SU2_CU(cudaMemcpyAsync(hist + 4 * (size_t)(c0 + first), h->d_hist, (size_t)(m - first) * 4 * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
     SU2_CU(cudaStreamSynchronize(h->stream));
   }
   h->sweep += (uint64_t)n;

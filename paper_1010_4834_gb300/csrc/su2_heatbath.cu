@@ -200,47 +200,6 @@ __global__ void __launch_bounds__(BS, Occ<P>::hb * kThreads / BS)
   }
 }
 
-// The plaquette after a measured sweep from the block sums of its three MEAS
-// substeps: meas[k * stride + b], k = 0, 1, 2 for MU = 1, 2, 3, b < nb[k].
-// One block; fixed-order compensated sums.  out = {all, spatial, space-time}
-// means of Tr/2 (Eq. 13).
-__global__ void __launch_bounds__(kThreads) k_plaquette_from_sweep(const double* meas, int stride, int nb1, int nb2,
-                                                                   int nb3, double volume, double* out) {
-  __shared__ double ss[kThreads / 32][3], sc[kThreads / 32][3];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nb[3] = {nb1, nb2, nb3};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    KSum a;
-    for (int b = threadIdx.x; b < nb[k]; b += kThreads) a.add(meas[(size_t)k * stride + b]);
-    a = warp_ksum(a);
-    if (lane == 0) {
-      ss[warp][k] = a.s;
-      sc[warp][k] = a.c;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      KSum a;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        KSum o;
-        o.s = ss[w][k];
-        o.c = sc[w][k];
-        a = ksum_combine(a, o);
-      }
-      tot[k] = a.value();
-    }
-    const double S = tot[0] + tot[1], T = tot[2];
-    const double n3 = 3.0 * volume;
-    out[0] = (S + T) / (2.0 * n3);
-    out[1] = S / n3;
-    out[2] = T / n3;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
@@ -277,13 +236,6 @@ cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint
     }
     if (e != cudaSuccess) return e;
   }));
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_plaquette_from_sweep(const double* meas, const int nb[3], int64_t volume, double* out,
-                                        cudaStream_t st) {
-  k_plaquette_from_sweep<<<1, kThreads, 0, st>>>(meas, kMeasStride, nb[0], nb[1], nb[2], (double)volume, out);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -46,15 +46,28 @@ cudaError_t launch_init(const LatticeView& v, int start, PhiloxKey key, uint32_t
 cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint32_t* sweep_base,
                             uint32_t sweep_off, const HBParams& hp, unsigned long long* stats,
                             cudaStream_t st, double* meas = nullptr, int* meas_blocks = nullptr);
-// Block sums of the three measuring substeps at meas + k * kMeasStride
-// (k = 0, 1, 2 for mu = 1, 2, 3; nb[k] blocks each) -> out[3] = plaquette
-// {all, spatial, space-time}.
+// Block sums of the three measuring substeps sit at meas + k * kMeasStride
+// (k = 0, 1, 2 for mu = 1, 2, 3; nb[k] blocks each).
 constexpr int kMeasStride = 8192;
-cudaError_t launch_plaquette_from_sweep(const double* meas, const int nb[3], int64_t volume, double* out,
-                                        cudaStream_t st);
+// Measured sweeps record {plaquette all, spatial, space-time, Polyakov} of
+// sweep s in row s mod kHistRing of a device ring, so that a run of them is
+// position-independent and replays as one CUDA graph.
+constexpr int kHistRing = 1024;
+// What the Polyakov kernel's last block does after a measured sweep: its
+// mean and the plaquette from the sweep's block sums go to row
+// (*sweep mod kHistRing) of hist, then *sweep is advanced by one.
+struct SweepEpilogue {
+  const double* meas;  // nullptr: no epilogue (the mean goes to out[0])
+  int nb[3];
+  double volume;
+  double* hist;
+  uint32_t* sweep;
+};
 cudaError_t launch_overrelax(const LatticeView& v, int mu, int parity, cudaStream_t st);
 cudaError_t launch_plaquette(const LatticeView& v, const Scratch& s, cudaStream_t st);
-cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t st);
+// With `ep` the reduction partials must not overlap ep->meas.
+cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t st,
+                            const SweepEpilogue* ep = nullptr);
 // APE: src has (at least) the 6 spatial classes; dst receives them.
 cudaError_t launch_ape(const LatticeView& src, void* dst, double alpha, cudaStream_t st);
 cudaError_t launch_copy_spatial(const LatticeView& src, void* dst, cudaStream_t st);

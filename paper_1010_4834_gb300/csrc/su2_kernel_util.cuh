@@ -145,6 +145,47 @@ __device__ __forceinline__ void final_sum(const double* partials, int nblocks, d
   }
 }
 
+// The plaquette after a measured sweep from the block sums of its three
+// plaquette-summing substeps: meas[k * stride + b], k = 0, 1, 2 for
+// mu = 1, 2, 3, b < nb[k].  Called by all kThreads threads of one block;
+// fixed-order compensated sums.  out = {all, spatial, space-time} means of
+// Tr/2 (Eq. 13).
+__device__ __forceinline__ void plaquette_from_block_sums(const double* meas, int stride, const int (&nb)[3],
+                                                          double volume, double* out) {
+  __shared__ double ss[kThreads / 32][3], sc[kThreads / 32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    KSum a;
+    for (int b = threadIdx.x; b < nb[k]; b += kThreads) a.add(__ldcg(meas + (size_t)k * stride + b));
+    a = warp_ksum(a);
+    if (lane == 0) {
+      ss[warp][k] = a.s;
+      sc[warp][k] = a.c;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      KSum a;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        KSum o;
+        o.s = ss[w][k];
+        o.c = sc[w][k];
+        a = ksum_combine(a, o);
+      }
+      tot[k] = a.value();
+    }
+    const double S = tot[0] + tot[1], T = tot[2];
+    const double n3 = 3.0 * volume;
+    out[0] = (S + T) / (2.0 * n3);
+    out[1] = S / n3;
+    out[2] = T / n3;
+  }
+}
+
 // Occupancy targets (blocks of 256 per SM) for the register-heavy kernels.
 #ifndef SU2_HB_MINB
 #define SU2_HB_MINB 4

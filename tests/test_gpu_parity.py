@@ -502,7 +502,7 @@ def test_sweep_measure_restart_and_launch_count():
     b = Lattice(dims, 2.3, seed=5, start="hot", prec="f64")
     n0 = kernel_launches()
     hist = a.sweep_measure(6)
-    assert kernel_launches() - n0 == 6 * (8 + 1 + 2)      # 8 substeps, counter, plaquette sum, Polyakov
+    assert kernel_launches() - n0 == 6 * (8 + 1)      # 8 substeps, Polyakov (+ plaquette, counter)
     ref = []
     for _ in range(6):
         b.sweep(1)
@@ -518,6 +518,38 @@ def test_sweep_measure_restart_and_launch_count():
     fresh = Lattice(dims, 2.3, seed=5, start="hot", prec="f64")
     assert np.array_equal(a.get_links(), fresh.get_links())
     for lat in (a, b, fresh):
+        lat.close()
+
+
+# Runs of 8 measured sweeps replay as a graph and write a history ring indexed
+# by the sweep counter: a run that starts 4 rows before the ring's end, wraps
+# and spans two host chunks (1024 rows each) must match sweep-by-sweep
+# measurements row for row, and leave the same links and counter.
+def test_sweep_measure_graph_ring_wrap_and_chunks():
+    from paper_1010_4834_gb300 import kernel_launches
+    dims = (4, 4, 4, 6)
+    a = Lattice(dims, 2.3, seed=9, start="hot", prec="f64")
+    b = Lattice(dims, 2.3, seed=9, start="hot", prec="f64")
+    a.sweep_count = 1020
+    b.sweep_count = 1020
+    n = 1030
+    n0 = kernel_launches()
+    hist = a.sweep_measure(n)
+    assert kernel_launches() - n0 == 9 * n
+    assert hist.shape == (n, 4)
+    rows = [0, 1, 3, 4, 5, 11, 12, 1023, 1024, 1025, n - 1]
+    ref = {}
+    for i in range(n):
+        b.sweep(1)
+        if i in rows:
+            ref[i] = list(b.plaquette()) + [b.polyakov()]
+    for i in rows:
+        np.testing.assert_allclose(hist[i, :3], ref[i][:3], rtol=0, atol=1e-14, err_msg="row %d" % i)
+        assert hist[i, 3] == ref[i][3], i
+    assert len(np.unique(hist[:, 3])) > n // 2      # every row was written
+    np.testing.assert_array_equal(a.get_links(), b.get_links())
+    assert a.sweep_count == b.sweep_count == 1020 + n
+    for lat in (a, b):
         lat.close()
 
 
