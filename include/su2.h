@@ -193,7 +193,8 @@ int su2_overrelax_sweep(su2_lattice* h, int n);
  * Mean plaquette (Section 2, Eqs. 12-13), as the mean of (1/2) Re Tr of the
  * plaquette: out[0] over all 6V plaquettes, out[1] over the 3V spatial ones,
  * out[2] over the 3V space-time ones.  1 on the cold start; the paper's
- * <P> per plaquette is 1 - out[0].  FP64 compensated accumulation.
+ * <P> per plaquette is 1 - out[0].  Per-thread sums (compensated in FP32),
+ * then FP64 block and final sums in a fixed order.
  * Synchronises.
  */
 int su2_plaquette(su2_lattice* h, double out[3]);

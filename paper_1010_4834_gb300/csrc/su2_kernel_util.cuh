@@ -44,16 +44,6 @@ template <> struct Acc<double> {
   __device__ __forceinline__ double value() const { return s; }
 };
 
-struct KSum {
-  double s = 0.0, c = 0.0;
-  __device__ __forceinline__ void add(double v) {
-    const double t = s + v;
-    c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return s + c; }
-};
-
 template <class T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -92,92 +82,53 @@ __device__ __forceinline__ bool block_partial(double (&v)[NV], double* partials,
   return last;
 }
 
-// Neumaier pairs combine as (a.s + b.s with its rounding error) + a.c + b.c.
-__device__ __forceinline__ KSum ksum_combine(KSum a, const KSum& b) {
-  a.add(b.s);
-  a.c += b.c;
-  return a;
+// Sum of one double over a block of kThreads threads, all of which call it;
+// the total is returned in thread 0.  Fixed-order trees over the lanes and
+// then the warps.  Plain FP64 adds: the terms are thread or block sums, and
+// their rounding (at most the term count times 2^-53 relative) stays far
+// below every tolerance, while a compensated pair costs several times as
+// many FP64 instructions, which GB300 issues at 1/64 of the FP32 rate: in
+// the one block that finishes a reduction that was 20 us per measured sweep.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sw[kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sw[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) t = warp_sum(lane < kThreads / 32 ? sw[lane] : 0.0);
+  __syncthreads();  // sw is free for the next call
+  return t;
 }
 
-// Fixed-order tree over the lanes of a warp; lane 0 ends with the total.
-__device__ __forceinline__ KSum warp_ksum(KSum a) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    KSum o;
-    o.s = __shfl_xor_sync(0xffffffffu, a.s, off);
-    o.c = __shfl_xor_sync(0xffffffffu, a.c, off);
-    a = ksum_combine(a, o);
-  }
-  return a;
-}
-
-// In the last block: tot[k] = sum over blocks of partials[b*NV + k].  Every
-// thread adds a strided subset (compensated), then a fixed-order tree over
-// lanes and warps combines them, so the result does not depend on timing and
-// no thread runs a long serial FP64 chain.
+// In the last block: tot[k] (thread 0) = sum over blocks of
+// partials[b*NV + k].  Every thread adds a strided subset, then block_sum,
+// so the result does not depend on timing.
 template <int NV>
 __device__ __forceinline__ void final_sum(const double* partials, int nblocks, double (&tot)[NV]) {
-  __shared__ double ss[kThreads / 32][NV], sc[kThreads / 32][NV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    KSum a;
-    for (int b = threadIdx.x; b < nblocks; b += kThreads) a.add(__ldcg(partials + (size_t)b * NV + k));
-    a = warp_ksum(a);
-    if (lane == 0) {
-      ss[warp][k] = a.s;
-      sc[warp][k] = a.c;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      KSum a;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        KSum o;
-        o.s = ss[w][k];
-        o.c = sc[w][k];
-        a = ksum_combine(a, o);
-      }
-      tot[k] = a.value();
-    }
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kThreads) a += __ldcg(partials + (size_t)b * NV + k);
+    tot[k] = block_sum(a);
   }
 }
 
 // The plaquette after a measured sweep from the block sums of its three
 // plaquette-summing substeps: meas[k * stride + b], k = 0, 1, 2 for
 // mu = 1, 2, 3, b < nb[k].  Called by all kThreads threads of one block;
-// fixed-order compensated sums.  out = {all, spatial, space-time} means of
-// Tr/2 (Eq. 13).
+// fixed-order sums.  out = {all, spatial, space-time} means of Tr/2
+// (Eq. 13), written by thread 0.
 __device__ __forceinline__ void plaquette_from_block_sums(const double* meas, int stride, const int (&nb)[3],
                                                           double volume, double* out) {
-  __shared__ double ss[kThreads / 32][3], sc[kThreads / 32][3];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double tot[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    KSum a;
-    for (int b = threadIdx.x; b < nb[k]; b += kThreads) a.add(__ldcg(meas + (size_t)k * stride + b));
-    a = warp_ksum(a);
-    if (lane == 0) {
-      ss[warp][k] = a.s;
-      sc[warp][k] = a.c;
-    }
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nb[k]; b += kThreads) a += __ldcg(meas + (size_t)k * stride + b);
+    tot[k] = block_sum(a);
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
-    double tot[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      KSum a;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        KSum o;
-        o.s = ss[w][k];
-        o.c = sc[w][k];
-        a = ksum_combine(a, o);
-      }
-      tot[k] = a.value();
-    }
     const double S = tot[0] + tot[1], T = tot[2];
     const double n3 = 3.0 * volume;
     out[0] = (S + T) / (2.0 * n3);

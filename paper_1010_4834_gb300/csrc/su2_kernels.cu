@@ -7,9 +7,9 @@
 // None of this work is a dense contraction (2x2 SU(2) products in
 // registers), so everything runs on the FP32/FP64 pipes; the sweep is bound
 // by HBM traffic and ALU issue.  Reductions are fused into the measurement
-// kernels: per-thread compensated sums, warp shuffles, one partial per block
-// and a last-block finisher that adds the partials in a fixed order, so a
-// result is reproducible run to run.
+// kernels: per-thread sums (compensated when the arithmetic is FP32), FP64
+// warp shuffles, one partial per block and a last-block finisher that adds
+// the partials in a fixed order, so a result is reproducible run to run.
 #include <atomic>
 #include <cfloat>
 
@@ -210,70 +210,70 @@ __global__ void __launch_bounds__(kThreads) k_plaquette(Links<P> L, Geom g, doub
 // time links in increasing t; mean of (1/2) Tr over the spatial sites.  Site
 // s = xs + Nsigma t has half-index (xs >> 1) + (Nsigma/2) t.
 //
-// The time links are read in chunks of C, and the loads of the next chunk are
-// issued before the products of the current one, so that every thread keeps
-// a chunk in flight while it multiplies (with one chunk at a time all threads
-// waited on memory together and then multiplied together, 55 us on 64^4
-// against 39 us for its 268 MB at the copy bandwidth).  After a measured
-// sweep the last block also finishes the sweep's plaquette, records both in
-// the history ring and advances the sweep counter (SweepEpilogue), which
-// saves two launches per sweep.
+// A block takes kThreads / G consecutive time lines, and each line is split
+// into G consecutive segments of nt / G >= 8 links (G a power of two <= 8
+// dividing nt, as large as that allows).  Warp group q loads segment q of
+// every line of the block in chunks of 8 (all loads of a chunk issued
+// before the products; each load instruction of a warp reads 32 consecutive
+// spatial sites at one t), and the segment products are multiplied in t
+// order through shared memory.  With one line per thread the kernel kept
+// one chunk in flight per thread at 120 registers and ran at under half the
+// copy bandwidth (ncu, 64^4: 24% warps active, long-scoreboard stalls 11 per
+// issue).  After a measured sweep the last block also finishes the sweep's
+// plaquette, records both in the history ring and advances the sweep
+// counter (SweepEpilogue), which saves two launches per sweep.
 // ---------------------------------------------------------------------------
-// FP64 loads whole chunks without the prefetch: its products are slow
-// enough to hide the loads, and the extra 16 doubles cut its occupancy
-// (48^4 measured sweep: 326 us over a plain one without, 373 with).
-template <int P> struct PolyChunk { static constexpr int value = 8; static constexpr bool pipe = true; };
-template <> struct PolyChunk<kF64> { static constexpr int value = 8; static constexpr bool pipe = false; };
+template <int P> struct PolyMinBlocks { static constexpr int value = 4; };
+template <> struct PolyMinBlocks<kF64> { static constexpr int value = 2; };
 
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_polyakov(Links<P, true> L, Geom g, double* partials,
-                                                       unsigned int* counter, double* out, SweepEpilogue ep) {
+__global__ void __launch_bounds__(kThreads, PolyMinBlocks<P>::value)
+    k_polyakov(Links<P, true> L, Geom g, int lg, double* partials, unsigned int* counter, double* out,
+               SweepEpilogue ep) {
   using R = typename Real<P>::T;
   using LT = Links<P, true>;
-  constexpr int C = PolyChunk<P>::value;
+  constexpr int C = 8;
+  __shared__ Quat<R> seg_prod[kThreads];
   Acc<R> acc;
   const int nsig = g.n[0] * g.n[1] * g.n[2];
   const uint32_t nsig_h = (uint32_t)(nsig / 2);
-  const int nt = g.n[3];
-  const int nfull = nt / C * C;
-  const int stride = gridDim.x * blockDim.x;
-  for (int xs = blockIdx.x * blockDim.x + threadIdx.x; xs < nsig; xs += stride) {
-    const Site x = site_from_index(g, (uint32_t)xs);
-    const int px = parity(x);
-    const uint32_t hh = (uint32_t)(xs >> 1);
-    // the time links of x alternate between the two parity classes: b0 holds
-    // those at even t, b1 those at odd t (C is even, so chunk offsets keep it)
-    const typename LT::E* b0 = px ? L.cls_base(7) : L.cls_base(6);
-    const typename LT::E* b1 = px ? L.cls_base(6) : L.cls_base(7);
+  const int G = 1 << lg;
+  const int lines = kThreads >> lg;  // lines per block, a multiple of 32
+  const int seg = g.n[3] >> lg;
+  const int q = threadIdx.x / lines;
+  const int l = threadIdx.x - q * lines;
+  const int t0 = q * seg;
+  for (int first = blockIdx.x * lines; first < nsig; first += gridDim.x * lines) {
+    const int xs = first + l;
     Quat<R> pr = qone<R>();
-    Quat<R> u[C];
-    if (PolyChunk<P>::pipe && nfull) {
+    if (xs < nsig) {
+      const Site x = site_from_index(g, (uint32_t)xs);
+      const uint32_t hh = (uint32_t)(xs >> 1);
+      // the time links of x alternate between the two parity classes: b0
+      // holds those at t of the parity of t0, b1 the others
+      const bool swap = (parity(x) ^ (t0 & 1)) != 0;
+      const typename LT::E* b0 = swap ? L.cls_base(7) : L.cls_base(6);
+      const typename LT::E* b1 = swap ? L.cls_base(6) : L.cls_base(7);
+      const uint32_t e0 = hh + nsig_h * (uint32_t)t0;
+      int t = 0;
+      for (; t + C <= seg; t += C) {
+        Quat<R> u[C];
 #pragma unroll
-      for (int j = 0; j < C; ++j) u[j] = LT::ldp((j & 1) ? b1 : b0, hh + nsig_h * (uint32_t)j);
-    }
-    for (int t = 0; t < nfull; t += C) {
-      if constexpr (PolyChunk<P>::pipe) {
-        Quat<R> nx[C];
-        const bool more = t + C < nfull;
-        if (more) {
-#pragma unroll
-          for (int j = 0; j < C; ++j) nx[j] = LT::ldp((j & 1) ? b1 : b0, hh + nsig_h * (uint32_t)(t + C + j));
-        }
-#pragma unroll
-        for (int j = 0; j < C; ++j) pr = qmul(pr, u[j]);
-        if (more) {
-#pragma unroll
-          for (int j = 0; j < C; ++j) u[j] = nx[j];
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < C; ++j) u[j] = LT::ldp((j & 1) ? b1 : b0, hh + nsig_h * (uint32_t)(t + j));
+        for (int j = 0; j < C; ++j) u[j] = LT::ldp((j & 1) ? b1 : b0, e0 + nsig_h * (uint32_t)(t + j));
 #pragma unroll
         for (int j = 0; j < C; ++j) pr = qmul(pr, u[j]);
       }
+      for (; t < seg; ++t) pr = qmul(pr, LT::ldp((t & 1) ? b1 : b0, e0 + nsig_h * (uint32_t)t));
     }
-    for (int t = nfull; t < nt; ++t) pr = qmul(pr, LT::ldp((t & 1) ? b1 : b0, hh + nsig_h * (uint32_t)t));
-    acc.add(pr.w);
+    if (G > 1) {
+      seg_prod[threadIdx.x] = pr;
+      __syncthreads();
+      if (q == 0) {
+        for (int k = 1; k < G; ++k) pr = qmul(pr, seg_prod[k * lines + l]);
+      }
+      __syncthreads();
+    }
+    if (q == 0 && xs < nsig) acc.add(pr.w);
   }
   double v[1] = {acc.value()};
   if (block_partial<1>(v, partials, counter)) {
@@ -686,28 +686,14 @@ __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, 
 template <int RC>
 __global__ void __launch_bounds__(kThreads) k_wilson_rt_final(const double* partials, int gx, int ntc, int tmax,
                                                               double inv, double* out) {
-  __shared__ double ss[kThreads / 32], sc[kThreads / 32];
   const int o = blockIdx.x;
   const int r = o / tmax, t = o % tmax;
   const int y = (r / RC) * ntc + t / kWrtT;
   const int slot = (r % RC) * kWrtT + t % kWrtT;
-  KSum a;
-  for (int bx = threadIdx.x; bx < gx; bx += blockDim.x)
-    a.add(__ldcg(partials + ((size_t)y * gx + bx) * (RC * kWrtT) + slot));
-  a = warp_ksum(a);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { ss[warp] = a.s; sc[warp] = a.c; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    KSum tot;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      KSum q;
-      q.s = ss[w];
-      q.c = sc[w];
-      tot = ksum_combine(tot, q);
-    }
-    out[o] = tot.value() * inv;
-  }
+  double a = 0.0;
+  for (int bx = threadIdx.x; bx < gx; bx += blockDim.x) a += __ldcg(partials + ((size_t)y * gx + bx) * (RC * kWrtT) + slot);
+  const double tot = block_sum(a);
+  if (threadIdx.x == 0) out[o] = tot * inv;
 }
 
 // out[(R-1) tmax + (T-1)]: one block per output adds the per-block sums of the
@@ -715,31 +701,18 @@ __global__ void __launch_bounds__(kThreads) k_wilson_rt_final(const double* part
 template <int TC>
 __global__ void __launch_bounds__(kThreads) k_wilson_final(const double* partials, int gx, int rmax, int tmax,
                                                            double inv, double* out) {
-  __shared__ double ss[kThreads / 32], sc[kThreads / 32];
   const int o = blockIdx.x;
   const int r = o / tmax, t = o % tmax;
   const int c = t / TC, j = t % TC;
   const int per = rmax * TC;
   const int n = 3 * gx;
-  KSum a;
+  double a = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int m = i / gx, bx = i % gx;
-    a.add(__ldcg(partials + (size_t)((3 * c + m) * gx + bx) * per + r * TC + j));
+    a += __ldcg(partials + (size_t)((3 * c + m) * gx + bx) * per + r * TC + j);
   }
-  a = warp_ksum(a);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { ss[warp] = a.s; sc[warp] = a.c; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    KSum tot;
-    for (int w = 0; w < kThreads / 32; ++w) {
-      KSum q;
-      q.s = ss[w];
-      q.c = sc[w];
-      tot = ksum_combine(tot, q);
-    }
-    out[o] = tot.value() * inv;
-  }
+  const double tot = block_sum(a);
+  if (threadIdx.x == 0) out[o] = tot * inv;
 }
 
 // ---------------------------------------------------------------------------
@@ -821,8 +794,12 @@ cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t
   SU2_DISPATCH(v.prec, {
     auto L = links_of<P, true>(v.links, v.g.vh);
     const int64_t nsig = 2 * v.g.vh / v.g.n[3];
-    const int gr = grid_for(k_polyakov<P>, nsig);
-    k_polyakov<P><<<gr, kThreads, 0, st>>>(L, v.g, s.partials, s.counter, s.out, e);
+    // segments per time line: the largest power of two <= 8 that divides nt
+    // and leaves segments of at least 8 links
+    int lg = 0;
+    while (lg < 3 && v.g.n[3] % (2 << lg) == 0 && v.g.n[3] / (2 << lg) >= 8) ++lg;
+    const int gr = grid_for(k_polyakov<P>, nsig << lg);
+    k_polyakov<P><<<gr, kThreads, 0, st>>>(L, v.g, lg, s.partials, s.counter, s.out, e);
   });
   count_launches(1);
   return cudaGetLastError();

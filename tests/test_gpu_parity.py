@@ -226,6 +226,24 @@ def test_measurements(dims, prec):
     lat.close()
 
 
+# Long time extents: each time line is split over a group of up to 32 lanes
+# (segments of >= 8 links) whose products are combined by shuffles in t
+# order.  nt = 16 .. 256 covers 2 .. 32 lanes, segments with a ragged chunk
+# (40: 4 x 10) and odd segment lengths (18: 2 x 9, 36: 4 x 9), where half
+# the segments start on an odd t.  Random fields: an out-of-order product
+# changes every line's trace.
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16q"])
+@pytest.mark.parametrize("nt", [16, 18, 24, 36, 40, 64, 256])
+def test_polyakov_long_time_extent(nt, prec):
+    dims = (2, 4, 2, nt)
+    U = inputs.random_field(dims, 31 + nt)
+    lat = Lattice(dims, 2.0, prec=prec)
+    lat.set_links(U)
+    ref = as_stored(U, prec)
+    assert abs(lat.polyakov() - oracle.polyakov(list(dims), ref)) < MTOL[prec]
+    lat.close()
+
+
 def test_measurements_on_thermalised_configuration():
     dims = (8, 8, 8, 8)
     lat = Lattice(dims, 2.5, seed=2, start="hot", prec="f64")
