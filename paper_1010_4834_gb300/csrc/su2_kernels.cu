@@ -307,21 +307,19 @@ __global__ void __launch_bounds__(kThreads, PolyMinBlocks<P>::value)
 // backward.  blockIdx.y = parity.
 // ---------------------------------------------------------------------------
 template <int P, int MU, int NU>
-__device__ __forceinline__ void ape_pair(const Links<P, true>& L, const Geom& g, const Site& x, int p,
+__device__ __forceinline__ void ape_pair(const Links<P, true>& L, int h, int p, const int (&dp)[3], const int (&dm)[3],
                                          const Quat<typename Real<P>::T>& umu, const Quat<typename Real<P>::T>& unu,
                                          Quat<typename Real<P>::T>& smu, Quat<typename Real<P>::T>& snu) {
   using R = typename Real<P>::T;
   const int q = p ^ 1;
-  const Quat<R> a = qmul_nd(L.ld(2 * NU + q, hidx(g, shifted<MU, +1>(g, x))), L.ld(2 * MU + q, hidx(g, shifted<NU, +1>(g, x))));
-  const Site xn = shifted<NU, -1>(g, x);   // x - nu
-  const Site xm = shifted<MU, -1>(g, x);   // x - mu
-  const int hn = hidx(g, xn), hm = hidx(g, xm);
+  const Quat<R> a = qmul_nd(L.ld(2 * NU + q, h + dp[MU]), L.ld(2 * MU + q, h + dp[NU]));
+  const int hn = h + dm[NU], hm = h + dm[MU];  // x - nu, x - mu
   // link mu, term nu: forward U_nu(x) A^dag, backward U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
   qacc_mul_nd(smu, unu, a);
-  qacc_mul(smu, qmul_dn(L.ld(2 * NU + q, hn), L.ld(2 * MU + q, hn)), L.ld(2 * NU + p, hidx(g, shifted<MU, +1>(g, xn))));
+  qacc_mul(smu, qmul_dn(L.ld(2 * NU + q, hn), L.ld(2 * MU + q, hn)), L.ld(2 * NU + p, hn + dp[MU]));
   // link nu, term mu: forward U_mu(x) A, backward U_mu(x-mu)^dag U_nu(x-mu) U_mu(x-mu+nu)
   qacc_mul(snu, umu, a);
-  qacc_mul(snu, qmul_dn(L.ld(2 * MU + q, hm), L.ld(2 * NU + q, hm)), L.ld(2 * MU + p, hidx(g, shifted<NU, +1>(g, xm))));
+  qacc_mul(snu, qmul_dn(L.ld(2 * MU + q, hm), L.ld(2 * NU + q, hm)), L.ld(2 * MU + p, hm + dp[NU]));
 }
 
 template <int P>
@@ -349,11 +347,15 @@ __device__ __forceinline__ void ape_sites(const Links<P, true>& src, const Links
   const int stride = gridDim.x * blockDim.x;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < vh; h += stride) {
     const Site x = site_from_half(g, (uint32_t)h, p);
+    // half-index steps to the six spatial neighbours; the index of x + a + b
+    // is h + step(a) + step(b) for steps in different directions
+    const int dp[3] = {half_step<0, +1>(g, x), half_step<1, +1>(g, x), half_step<2, +1>(g, x)};
+    const int dm[3] = {half_step<0, -1>(g, x), half_step<1, -1>(g, x), half_step<2, -1>(g, x)};
     const Quat<R> u0 = src.ld(0 + p, h), u1 = src.ld(2 + p, h), u2 = src.ld(4 + p, h);
     Quat<R> s0 = qmake<R>(0, 0, 0, 0), s1 = s0, s2 = s0;
-    ape_pair<P, 0, 1>(src, g, x, p, u0, u1, s0, s1);
-    ape_pair<P, 0, 2>(src, g, x, p, u0, u2, s0, s2);
-    ape_pair<P, 1, 2>(src, g, x, p, u1, u2, s1, s2);
+    ape_pair<P, 0, 1>(src, h, p, dp, dm, u0, u1, s0, s1);
+    ape_pair<P, 0, 2>(src, h, p, dp, dm, u0, u2, s0, s2);
+    ape_pair<P, 1, 2>(src, h, p, dp, dm, u1, u2, s1, s2);
     ape_store<P>(dst, 0 + p, h, u0, s0, c0, c1);
     ape_store<P>(dst, 2 + p, h, u1, s1, c0, c1);
     ape_store<P>(dst, 4 + p, h, u2, s2, c0, c1);
