@@ -153,7 +153,12 @@ int su2_restart(su2_lattice* h, int start);
  * counter by n.  The plaquette is summed inside the sweep (in the
  * odd-parity substeps of mu = 1, 2, 3, from their staples), so it equals
  * su2_plaquette of the new configuration up to the order of summation; the
- * links are the same as after su2_heatbath_sweep.
+ * Polyakov loop equals su2_polyakov; the links are the same as after
+ * su2_heatbath_sweep.  A measured sweep is nine launches (eight substeps and
+ * the Polyakov kernel, which also finishes the plaquette and advances the
+ * device sweep counter); runs of eight replay from a cached CUDA graph that
+ * su2_set_beta and su2_set_options drop.  hist is caller-owned host memory
+ * of 4 n doubles; n < 0, or hist NULL with n > 0, returns SU2_EINVAL.
  */
 int su2_sweep_measure(su2_lattice* h, int n, double* hist);
 
