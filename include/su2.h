@@ -255,11 +255,14 @@ int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smeared, double
  * precision (F16Q rounds to binary16), invalidates the smeared copy and keeps
  * the sweep counter.  Both synchronise.  set_links from page-locked host
  * memory (cudaHostAlloc, cudaHostRegister) lets the conversion kernel read
- * the host buffer directly; everything else goes through a device staging
- * buffer in chunks.
+ * the host buffer directly; set_links also takes device (or managed) memory
+ * of the handle's device in the same layout, which the conversion kernel
+ * reads on the handle's stream (the caller makes sure it is ready there,
+ * e.g. filled by an earlier copy on that stream or after an event wait);
+ * pageable host memory goes through a device staging buffer in chunks.
  */
 int su2_get_links(su2_lattice* h, double* host);
-int su2_set_links(su2_lattice* h, const double* host);
+int su2_set_links(su2_lattice* h, const double* links);
 
 /*
  * The links of sites [first, first + count) (lexicographic site index, as in

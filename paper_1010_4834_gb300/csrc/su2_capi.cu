@@ -596,13 +596,25 @@ extern "C" int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smea
 // The device-visible address of page-locked host memory (cudaHostAlloc,
 // cudaHostRegister: the conversion kernel then reads it directly over the
 // host link, at the copy engine's rate), or NULL for pageable memory.
-static void* host_mapped(const void* host) {
+// The address a kernel on `device` reads `p` through: page-locked host memory
+// (mapped), or device / managed memory of that device; nullptr for pageable
+// host memory.  *other_device is set for device memory of another GPU.
+static void* device_readable(const void* p, int device, bool* other_device) {
+  *other_device = false;
   cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+  if (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged) return a.devicePointer;
+  if (a.type == cudaMemoryTypeDevice) {
+    if (a.device != device) {
+      *other_device = true;
+      return nullptr;
+    }
+    return a.devicePointer;
+  }
+  return nullptr;
 }
 
 // Sites [first, first + count) in canonical FP64 order into host[16 * count],
@@ -636,17 +648,20 @@ extern "C" int su2_get_sites(su2_lattice* h, int64_t first, int64_t count, doubl
   return copy_sites_out(h, first, count, host);
 }
 
-extern "C" int su2_set_links(su2_lattice* h, const double* host) {
+extern "C" int su2_set_links(su2_lattice* h, const double* links) {
   clear_error();
-  if (!h || !host) return fail(SU2_EINVAL, "NULL argument");
+  if (!h || !links) return fail(SU2_EINVAL, "NULL argument");
   DeviceGuard dg(h->device);
   const int64_t V = 2 * h->g.vh;
-  if (const void* d = host_mapped(host)) {
+  bool other = false;
+  const void* d = device_readable(links, h->device, &other);
+  if (other) return fail(SU2_EINVAL, "links are in the memory of another device");
+  if (d) {
     SU2_CU(launch_from_canonical(view(h), static_cast<const double*>(d), 0, V, h->stream));
   } else {
     for (int64_t s0 = 0; s0 < V; s0 += h->staging_sites) {
       const int64_t ns = V - s0 < h->staging_sites ? V - s0 : h->staging_sites;
-      SU2_CU(cudaMemcpyAsync(h->staging, host + 16 * s0, (size_t)ns * 16 * sizeof(double),
+      SU2_CU(cudaMemcpyAsync(h->staging, links + 16 * s0, (size_t)ns * 16 * sizeof(double),
                              cudaMemcpyHostToDevice, h->stream));
       SU2_CU(launch_from_canonical(view(h), h->staging, s0, ns, h->stream));
     }

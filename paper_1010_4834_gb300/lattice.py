@@ -181,6 +181,14 @@ class Lattice:
         return out
 
     def set_links(self, U):
+        """Canonical FP64 links (V, 4, 4) from a numpy array, or from a
+        contiguous float64 CUDA tensor on the lattice's device, which must be
+        ready on the lattice's stream (the library reads it there)."""
+        if hasattr(U, "is_cuda") and U.is_cuda:
+            import torch
+            assert U.dtype == torch.float64 and U.is_contiguous() and U.numel() == self.volume * 16
+            check(_lib.load().su2_set_links(self._h, C.cast(C.c_void_p(U.data_ptr()), C.POINTER(C.c_double))))
+            return
         U = np.ascontiguousarray(U, np.float64)
         assert U.size == self.volume * 16
         check(_lib.load().su2_set_links(self._h, _dptr(U)))

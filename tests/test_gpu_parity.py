@@ -110,6 +110,24 @@ def test_pinned_host_buffers_take_the_direct_path(prec):
     b.close()
 
 
+def test_set_links_from_device_memory():
+    # a float64 CUDA tensor in the canonical layout is read on the device by
+    # the conversion kernel; the result equals the host path bit for bit
+    import torch
+    dims = (8, 6, 4, 10)
+    U = inputs.random_field(dims, 23)
+    for prec in ("f64", "f32", "f16q"):
+        a = Lattice(dims, 2.0, prec=prec)
+        b = Lattice(dims, 2.0, prec=prec)
+        d = torch.from_numpy(U.copy()).cuda()
+        torch.cuda.current_stream().synchronize()
+        a.set_links(d)
+        b.set_links(U)
+        np.testing.assert_array_equal(a.get_links(), b.get_links())
+        a.close()
+        b.close()
+
+
 # ---------------------------------------------------------------------------
 def substep_compare(dims, prec, beta, U0, mu, p, sweep, sampler="kp", max_tries=64, seed=7):
     lat = Lattice(dims, beta, seed=seed, prec=prec)
