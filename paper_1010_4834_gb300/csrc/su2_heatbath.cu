@@ -2,6 +2,8 @@
 // Section 4), with its optional plaquette sum for measured sweeps, and the
 // kernel that turns those sums into the plaquette.  Paper: Cardoso & Bicudo,
 // arXiv:1010.4834.
+#include <type_traits>
+
 #include "su2_internal.h"
 #include "su2_kernel_util.cuh"
 
@@ -40,7 +42,12 @@ namespace su2 {
 // 48^4 (17 k per SM) 256 is faster (70.9 against 72.2 us; 16^4 12.3
 // against 14.0), as more, smaller blocks spread the few block iterations
 // evenly over the SMs.  The switch is at SU2_HB_BIG_PER_SM half-lattice
-// sites per SM.  FP64 needs 128 registers a thread, so 256 always.
+// sites per SM.  FP64 needs 128 registers a thread, so never 1024; FP64
+// lattices with fewer than two blocks of 256 per SM run blocks of 64 so
+// that their few warps land on as many SMs as possible, since each SM's FP64
+// pipe issues at 1/64 of the FP32 rate: on 8^4 (2048 links per substep)
+// 256-thread blocks fill 8 SMs (measured sweep 344 us, 235 with blocks of
+// 64).  FP32 gains nothing from it (32^3 x 4 plain sweep 32.4 -> 34.0 us).
 #ifndef SU2_HB_BIG_PER_SM
 #define SU2_HB_BIG_PER_SM 32768
 #endif
@@ -211,28 +218,33 @@ cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint
     // direction and parity are template parameters, so every class index in
     // the kernel is a compile-time constant: per-class base pointers
     auto L = links_of<P, true>(v.links, v.g.vh);
-    const bool big = P != kF64 && v.g.vh >= (int64_t)SU2_HB_BIG_PER_SM * device_info().sms;
-    auto launch = [&](auto kernel, int bs, double* m) -> cudaError_t {
-      const int gr = grid_for(kernel, v.g.vh, 0, bs);
+    const int64_t sms = device_info().sms;
+    const int bs = P != kF64 ? (v.g.vh >= (int64_t)SU2_HB_BIG_PER_SM * sms ? 1024 : 256)
+                             : (v.g.vh >= 2 * 256 * sms ? 256 : 64);
+    auto launch = [&](auto kernel, int nthreads, double* m) -> cudaError_t {
+      const int gr = grid_for(kernel, v.g.vh, 0, nthreads);
       if (m) {
         if (gr > kMeasStride) return cudaErrorInvalidConfiguration;
         *meas_blocks = gr;
       }
-      kernel<<<gr, bs, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, stats, m);
+      kernel<<<gr, nthreads, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, stats, m);
       return cudaSuccess;
+    };
+    // block sizes per precision: FP64 256 or 64, FP32 / F16Q 1024 or 256
+    auto with_bs = [&](auto meas_c, auto par_c, double* m) -> cudaError_t {
+      constexpr bool M = decltype(meas_c)::value;
+      constexpr int PP = decltype(par_c)::value;
+      constexpr int kSmall = P == kF64 ? 64 : 256, kLarge = P == kF64 ? 256 : 1024;
+      return bs == kLarge ? launch(k_heatbath<P, MU, M, PP, kLarge>, kLarge, m)
+                          : launch(k_heatbath<P, MU, M, PP, kSmall>, kSmall, m);
     };
     cudaError_t e = cudaSuccess;
     if (meas) {
-      if constexpr (MU >= 1) {
-        e = big ? launch(k_heatbath<P, MU, true, 1, (P == kF64 ? 256 : 1024)>, P == kF64 ? 256 : 1024, meas)
-                : launch(k_heatbath<P, MU, true, 1, 256>, 256, meas);
-      }
+      if constexpr (MU >= 1) e = with_bs(std::true_type{}, std::integral_constant<int, 1>{}, meas);
     } else if (parity == 0) {
-      e = big ? launch(k_heatbath<P, MU, false, 0, (P == kF64 ? 256 : 1024)>, P == kF64 ? 256 : 1024, nullptr)
-              : launch(k_heatbath<P, MU, false, 0, 256>, 256, nullptr);
+      e = with_bs(std::false_type{}, std::integral_constant<int, 0>{}, nullptr);
     } else {
-      e = big ? launch(k_heatbath<P, MU, false, 1, (P == kF64 ? 256 : 1024)>, P == kF64 ? 256 : 1024, nullptr)
-              : launch(k_heatbath<P, MU, false, 1, 256>, 256, nullptr);
+      e = with_bs(std::false_type{}, std::integral_constant<int, 1>{}, nullptr);
     }
     if (e != cudaSuccess) return e;
   }));
