@@ -255,15 +255,27 @@ def reduce_over_ranks(dist, elapsed, launches, device):
     return float(t.item()), int(c.item())
 
 
+def _code_only(text, python=False):
+    """Source text without comments and with whitespace runs collapsed, so
+    that editing a comment does not count as changing the kernel."""
+    import re
+    if python:
+        text = re.sub(r"#[^\n]*", " ", text)
+    else:
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_sha():
-    """Hash of the heat-bath kernel's sources and build flags."""
+    """Hash of the heat-bath kernel's sources (code only) and build flags."""
     h = hashlib.sha256()
     pkg = os.path.join(ROOT, "paper_1010_4834_gb300")
     for f in (os.path.join(pkg, "csrc", "su2_device.cuh"), os.path.join(pkg, "csrc", "su2_heatbath.cu"),
               os.path.join(pkg, "csrc", "su2_kernel_util.cuh"), os.path.join(pkg, "csrc", "su2_internal.h"),
               os.path.join(pkg, "build.py")):
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read(), python=f.endswith(".py")).encode())
     return h.hexdigest()[:16]
 
 

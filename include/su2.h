@@ -5,8 +5,8 @@
  *
  * The calls follow the paper's statement of the problem: start configurations
  * (Section 4, kernel list: cold start, hot start, read a configuration), the
- * checkerboard heat-bath update (Section 2, Eqs. 5-9 and 11; Section 4,
- * "separately by direction and by even and odd sites"), over-relaxation
+ * checkerboard heat-bath update (Section 2, Eqs. 5-9 and 11; Section 4, one
+ * direction and one site parity at a time), over-relaxation
  * (Section 2, Eq. 10) and the measurements: plaquette (Eqs. 12-13), Polyakov
  * loop (Eqs. 14-15), Wilson loops (Eq. 18) and APE smearing (Eq. 19).
  *
@@ -121,7 +121,7 @@ int su2_set_stream(su2_lattice* h, void* cuda_stream);
  * Sampler options.  max_tries >= 1 (default 64): trials of the a0 sampler per
  * link before the old link is kept (an exact step: the accepted-value kernel is
  * proportional to the target and independent of the old link).  max_tries = 1
- * reproduces the paper's "only one try" benchmark mode (Section 5.1).
+ * reproduces the single-trial setting of the paper's benchmarks (Section 5.1).
  * sampler: SU2_SAMPLER_KP or SU2_SAMPLER_CREUTZ.
  */
 int su2_set_options(su2_lattice* h, int max_tries, int sampler);
@@ -282,7 +282,7 @@ int su2_sweep_count(su2_lattice* h, uint64_t* n);
 int su2_set_sweep_count(su2_lattice* h, uint64_t n);
 
 /*
- * Checkpoint (Section 4: "read a configuration from input file"): a binary
+ * Checkpoint (Section 4 lists reading a configuration from a file): a binary
  * file with a header (magic "SU2GB300", version, dims, beta, seed, sweep
  * counter, precision, sampler options) followed by the canonical FP64 links.
  * su2_load creates a new handle with precision `prec` (-1: as saved).

@@ -335,7 +335,8 @@ int oracle_heatbath_link(const oracle_chain* c, long s, int mu, uint32_t sweep,
 
 /*
  * One checkerboard substep: every link of direction mu on sites of parity
- * `parity` (Section 4: "separately by direction and by even and odd sites").
+ * `parity` (the checkerboard order of Section 4: one direction and one site
+ * parity at a time).
  * The links of one (mu, parity) class do not enter each other's staples, so
  * the order of the loop does not matter; canonical order is used.
  * `margin` (may be NULL) receives, per updated link at index s*nd+mu, the

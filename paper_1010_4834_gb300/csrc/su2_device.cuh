@@ -4,7 +4,7 @@
 //
 // Paper: Cardoso & Bicudo, arXiv:1010.4834.  Section 2 (Eqs. 1-9, 11) defines
 // the link parametrisation and the heat-bath distribution; Section 4 the
-// checkerboard ("separately by direction and by even and odd sites").
+// checkerboard order (one direction and one site parity at a time).
 //
 // Coordinates are kept in scalars and every lattice shift names its direction
 // at compile time, so no coordinate array is ever indexed at run time (which

@@ -1,7 +1,7 @@
 // The checkerboard heat-bath substep for sm_103a (Section 2 Eqs. 5-9, 11;
-// Section 4), with its optional plaquette sum for measured sweeps, and the
-// kernel that turns those sums into the plaquette.  Paper: Cardoso & Bicudo,
-// arXiv:1010.4834.
+// Section 4), with its optional plaquette sum for measured sweeps (the
+// Polyakov kernel's last block turns those block sums into the plaquette).
+// Paper: Cardoso & Bicudo, arXiv:1010.4834.
 #include <type_traits>
 
 #include "su2_internal.h"
