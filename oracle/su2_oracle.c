@@ -178,7 +178,7 @@ static void haar_from_uniforms(const double u[4], double q[4]) {
   for (int i = 0; i < 4; i++) q[i] = z[i] / n;
 }
 
-/* Hot start: "random SU(2) matrix" on every link (Section 4, kernel list),
+/* Hot start: a random SU(2) element on every link (Section 4, kernel list),
  * read as a Haar-distributed element per link, from Philox draw 0 of the
  * reserved sweep index 0xFFFFFFFF. */
 void oracle_hot_link(const oracle_chain* c, long s, int mu, double q[4]) {

@@ -72,7 +72,7 @@ size_t scratch_bytes() {
 
 // ---------------------------------------------------------------------------
 // Start configurations (Section 4 kernel list: cold start U = 1, hot start a
-// random SU(2) matrix, read here as Haar via Philox draw 0 of sweep index
+// random element of SU(2) on every link, read here as Haar via Philox draw 0 of sweep index
 // 0xFFFFFFFF).  One thread per (site, direction).
 // ---------------------------------------------------------------------------
 template <int P>
