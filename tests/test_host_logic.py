@@ -1,0 +1,60 @@
+"""Host-side logic with no GPU: ensemble statistics and the benchmark's
+source hash that ties the committed ncu traffic to the profiled kernel."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_1010_4834_gb300 import ensemble  # noqa: E402
+
+
+def test_binned_mean_and_error_of_independent_draws():
+    # independent normal draws: the binned error is the standard error of
+    # the mean, sigma / sqrt(n), whatever the bin count
+    rng = np.random.default_rng(3)
+    x = rng.normal(2.0, 0.5, 200_000)
+    for nbins in (10, 20, 50):
+        m, e = ensemble.binned(x, nbins)
+        assert abs(m - 2.0) < 5 * 0.5 / np.sqrt(len(x))
+        assert 0.6 < e / (0.5 / np.sqrt(len(x))) < 1.6
+
+
+def test_binned_error_grows_with_autocorrelation():
+    # AR(1) series with rho = 0.9: the true error of the mean is larger than
+    # the naive one by sqrt((1 + rho) / (1 - rho)) = sqrt(19); long bins see it
+    rng = np.random.default_rng(4)
+    n, rho = 400_000, 0.9
+    eps = rng.normal(0.0, 1.0, n)
+    x = np.empty(n)
+    x[0] = eps[0]
+    for i in range(1, n):
+        x[i] = rho * x[i - 1] + np.sqrt(1 - rho * rho) * eps[i]
+    _, e = ensemble.binned(x, 20)
+    naive = 1.0 / np.sqrt(n)
+    assert 0.6 * np.sqrt(19) < e / naive < 1.5 * np.sqrt(19)
+
+
+def test_binned_drops_the_ragged_tail():
+    x = np.arange(23, dtype=float)          # 20 used in 10 bins of 2, 3 dropped
+    m, _ = ensemble.binned(x, 10)
+    assert m == np.arange(20).mean()
+
+
+def test_deviation_in_combined_errors():
+    assert ensemble.deviation((1.0, 0.3), (0.5, 0.4)) == (0.5 / 0.5)
+    assert ensemble.deviation((0.5, 0.3), (1.0, 0.4)) == -1.0
+
+
+def test_source_hash_ignores_comments_and_follows_code():
+    import bench
+    c = "int f(int a) { return a + 1; } // add one\n/* block\n comment */\n"
+    assert bench._code_only(c) == bench._code_only(c.replace("add one", "increment").replace("block", "x"))
+    assert bench._code_only(c) != bench._code_only(c.replace("a + 1", "a + 2"))
+    p = "x = 1  # one\ny = x // 2\n"
+    assert bench._code_only(p, python=True) == bench._code_only(p.replace("# one", "# first"), python=True)
+    assert bench._code_only(p, python=True) != bench._code_only(p.replace("// 2", "// 3"), python=True)
+    sha = bench.source_sha()
+    assert len(sha) == 16 and all(ch in "0123456789abcdef" for ch in sha)
