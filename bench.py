@@ -307,18 +307,20 @@ def measured_peaks():
 
 
 def cpu_baseline():
-    """The oracle as it stands (single thread, FP64) on one heat-bath substep
-    of the same 64^4 lattice."""
+    """The oracle as it stands (single thread, FP64) on the first four
+    heat-bath substeps (half a sweep) of the same 64^4 lattice."""
     import oracle
     ch = oracle.chain(BETA, seed=1)
     U = oracle.init_hot(list(DIMS), ch)
+    updates = 0
     t0 = time.perf_counter()
-    st = oracle.substep(list(DIMS), U, ch, 0, 0, 0)
+    for k in range(4):
+        updates += oracle.substep(list(DIMS), U, ch, 0, k // 2, k % 2).updates
     t = time.perf_counter() - t0
-    return {"value": st.updates / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one heat-bath substep (mu=0, even sites: %d link updates) of the %s beta=2.6 "
-                      "hot-start lattice, plain FP64 C, single thread; %.1f s"
-                      % (st.updates, "x".join(map(str, DIMS)), t)}
+    return {"value": updates / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "the first four heat-bath substeps (mu = 0, 1; both parities: %d link updates) of the %s "
+                      "beta=2.6 hot-start lattice, plain FP64 C, single thread; %.1f s"
+                      % (updates, "x".join(map(str, DIMS)), t)}
 
 
 def run_gpu(args):
