@@ -75,8 +75,6 @@ namespace {
 constexpr int kGraphSweeps = 8;
 constexpr int64_t kStagingSites = (int64_t)1 << 18;
 
-constexpr int kHistSweeps = kHistRing;
-
 struct Layout {
   size_t links, ape0, ape1, partials, counter, out, state, hist, staging, total;
 };
@@ -95,7 +93,7 @@ Layout layout_for(const int dims[4], int prec) {
   L.counter = o; o = align256(o + 64 * sizeof(unsigned int));
   L.out = o; o = align256(o + kScratchOut * sizeof(double));
   L.state = o; o = align256(o + 256);
-  L.hist = o; o = align256(o + (size_t)kHistSweeps * 4 * sizeof(double));
+  L.hist = o; o = align256(o + (size_t)kHistRing * 4 * sizeof(double));
   const int64_t st = V < kStagingSites ? V : kStagingSites;
   L.staging = o; o = align256(o + (size_t)st * 16 * sizeof(double));
   L.total = o;
@@ -403,8 +401,8 @@ extern "C" int su2_sweep_measure(su2_lattice* h, int n, double* hist) {
   if (n > 0 && !hist) return fail(SU2_EINVAL, "hist is NULL");
   if (h->sweep + (uint64_t)n >= 0xFFFFFFFFull) return fail(SU2_EINVAL, "sweep counter would reach the reserved index 2^32 - 1");
   DeviceGuard dg(h->device);
-  for (int c0 = 0; c0 < n; c0 += kHistSweeps) {
-    const int m = n - c0 < kHistSweeps ? n - c0 : kHistSweeps;
+  for (int c0 = 0; c0 < n; c0 += kHistRing) {
+    const int m = n - c0 < kHistRing ? n - c0 : kHistRing;
     int left = m;
     if (left >= kGraphSweeps) {
       if (!h->mgraph) {
