@@ -58,3 +58,23 @@ def test_source_hash_ignores_comments_and_follows_code():
     assert bench._code_only(p, python=True) != bench._code_only(p.replace("// 2", "// 3"), python=True)
     sha = bench.source_sha()
     assert len(sha) == 16 and all(ch in "0123456789abcdef" for ch in sha)
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the oracle arm of the benchmark (CPU only), on a small extent so the
+    # test is quick: one JSON line with the keys the benchmark contract needs
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--extent", "8"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert "workload" in d["config"]
