@@ -37,6 +37,7 @@ _up = C.POINTER(C.c_uint32)
 def _load(path):
     L = C.CDLL(path)
     sig = {
+        "oracle_threads": (C.c_int, []),
         "oracle_philox4x32_10": (None, [_up, _up, _up]),
         "oracle_u01": (C.c_double, [C.c_uint32, C.c_int]),
         "oracle_draw": (None, [C.POINTER(Chain), C.c_long, C.c_int, C.c_uint32, C.c_uint32, _dp]),
@@ -74,6 +75,20 @@ def lib():
     if _lib is None:
         _lib = _load(_build.build())
     return _lib
+
+
+def threads():
+    """Threads the bound build's substep loop uses (1 for the serial build)."""
+    return lib().oracle_threads()
+
+
+@contextlib.contextmanager
+def parallel():
+    """Bind this module to the OpenMP build of the same source (all host
+    cores share the sites of each substep; results are those of the serial
+    build) for the duration of the block."""
+    with using_library(_build.build(omp=True)):
+        yield
 
 
 @contextlib.contextmanager

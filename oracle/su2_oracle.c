@@ -13,6 +13,19 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads a substep uses: 1 in the serial build, the OpenMP team size in
+ * the all-cores build. */
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 /* ======================================================================== */
 /* Random numbers                                                            */
@@ -338,13 +351,18 @@ int oracle_heatbath_link(const oracle_chain* c, long s, int mu, uint32_t sweep,
  * `parity` (the checkerboard order of Section 4: one direction and one site
  * parity at a time).
  * The links of one (mu, parity) class do not enter each other's staples, so
- * the order of the loop does not matter; canonical order is used.
+ * the order of the loop does not matter; canonical order is used.  For the
+ * same reason the sites may be shared among threads: built with OpenMP (the
+ * all-cores CPU baseline), the loop runs on every host core and leaves the
+ * same links and counts as the serial build, which ignores the pragma.
  * `margin` (may be NULL) receives, per updated link at index s*nd+mu, the
  * decision margin of oracle_sample_a0.
  */
 void oracle_substep(int nd, const int* dims, double* U, const oracle_chain* c, uint32_t sweep,
                     int mu, int parity, oracle_stats* st, double* margin) {
   long vol = oracle_volume(nd, dims);
+  uint64_t updates = 0, trials = 0, capped = 0, haar = 0;
+#pragma omp parallel for schedule(static) reduction(+ : updates, trials, capped, haar)
   for (long s = 0; s < vol; s++) {
     if (parity_of(nd, dims, s) != parity) continue;
     double sigma[4], nl[4], m = INFINITY;
@@ -353,12 +371,16 @@ void oracle_substep(int nd, const int* dims, double* U, const oracle_chain* c, u
     int n = oracle_heatbath_link(c, s, mu, sweep, sigma, l, nl, &m);
     for (int i = 0; i < 4; i++) l[i] = nl[i];
     if (margin) margin[(size_t)s * nd + mu] = m;
-    if (st) {
-      st->updates++;
-      if (n > 0) st->trials += (uint64_t)n;
-      if (n == 0) { st->capped++; st->trials += (uint64_t)c->max_tries; }
-      if (n < 0) st->haar++;
-    }
+    updates++;
+    if (n > 0) trials += (uint64_t)n;
+    if (n == 0) { capped++; trials += (uint64_t)c->max_tries; }
+    if (n < 0) haar++;
+  }
+  if (st) {
+    st->updates += updates;
+    st->trials += trials;
+    st->capped += capped;
+    st->haar += haar;
   }
 }
 

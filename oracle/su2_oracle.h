@@ -51,6 +51,9 @@ typedef struct {
   uint64_t haar;        /* links drawn from the Haar measure (alpha ~ 0)     */
 } oracle_stats;
 
+/* Threads the substep loop runs on (1 unless built with OpenMP). */
+int oracle_threads(void);
+
 /* --- random numbers ---------------------------------------------------- */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double oracle_u01(uint32_t x, int u23);
