@@ -45,6 +45,7 @@ SWEEPS = 100
 APE_STEPS, APE_ALPHA = 25, 0.7
 RMAX = TMAX = 16
 WORKLOAD = "su2_64^4_f32_beta2.6_hot_100sweeps_plaq_poly_ape25_W16x16"
+PREC = "f32"
 BATCH_SHAPES = [(8, 8, 8, 8)] * 16 + [(12, 12, 12, 12)] * 16 + [(16, 16, 16, 16)] * 16 + [(24, 24, 24, 6)] * 16
 
 
@@ -200,6 +201,25 @@ def small_configs(torch):
                     "32^3x4 scan the wall time of its 16 chains run concurrently on 16 streams"}
 
 
+def static_potential_run():
+    """Section 5.4 on the 16^4 beta = 2.5 configuration: 200 configurations
+    ten sweeps apart after 300 thermalisation sweeps, each smeared by 25 APE
+    steps (alpha = 0.7) before W(R, T <= 8); V(R) at its plateau in T and the
+    fitted string tension with jackknife errors, beside the paper's table."""
+    from paper_1010_4834_gb300 import Lattice, potential
+    lat = Lattice((16, 16, 16, 16), 2.5, seed=1, start="hot", prec="f32")
+    lat.sweep(300)
+    W = potential.wilson_ensemble(lat, 200, 10, alpha=0.7, n_ape=25, rmax=8, tmax=8)
+    lat.close()
+    res = potential.static_potential(W, rfit=6)
+    return {"lattice": "16^4", "beta": 2.5, "configurations": 200, "sweeps_apart": 10,
+            "ape": [25, 0.7], "V": [round(float(v), 5) for v in res["V"]],
+            "dV": [round(float(v), 5) for v in res["dV"]], "T_plateau": [int(t) for t in res["T_plateau"]],
+            "fit_R": [1, int(res["rfit"])], "sigma_a2": res["sigma_a2"], "sigma_a2_err": res["sigma_a2_err"],
+            "a_fm": res["a_fm"], "a_fm_err": res["a_fm_err"],
+            "paper_beta2.5": {"sigma_a2": 0.036623, "a_fm": 0.085682, "lattice": "24^3x32", "configurations": 1981}}
+
+
 def timed_sweeps(torch, lat, n, reps=3):
     """Device time of n heat-bath sweeps (graph path), best of reps."""
     best = None
@@ -298,6 +318,38 @@ def profiled_traffic(updates_per_launch):
         return None
 
 
+def profiled_f64_flops():
+    """FP64 flops per heat-bath link update (2 DFMA + DMUL + DADD thread
+    instructions, from the committed ncu summary of an FP64 substep), or None
+    if the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "hb_substep_f64.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != source_sha():
+        return None
+    try:
+        return float(vals["fp64_flops_per_update"])
+    except (KeyError, ValueError):
+        return None
+
+
+def f64_roofline(updates_per_s, fp64_peak):
+    """The FP64 heat bath against the probe-measured FP64 FMA rate (its bound:
+    GB300 issues FP64 at 1/64 of the FP32 rate)."""
+    fl = profiled_f64_flops()
+    if fl is None or not fp64_peak:
+        return {"bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "FLOP/s", "frac": None,
+                "note": "FP64 flops per update not profiled for this source"}
+    ach = fl * updates_per_s
+    return {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "FLOP/s", "frac": round(ach / fp64_peak, 4),
+            "flops_per_update": fl, "peak_kind": "measured (su2_probe_fma, FP64)"}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -306,21 +358,39 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def cpu_baseline():
-    """The oracle as it stands (single thread, FP64) on the first four
-    heat-bath substeps (half a sweep) of the same 64^4 lattice."""
+def _oracle_substeps(nsub):
+    """Time `nsub` heat-bath substeps of the oracle (in sweep order) on the
+    benchmark's hot-start lattice with the oracle build currently bound;
+    returns (link updates, seconds)."""
     import oracle
     ch = oracle.chain(BETA, seed=1)
     U = oracle.init_hot(list(DIMS), ch)
     updates = 0
     t0 = time.perf_counter()
-    for k in range(4):
-        updates += oracle.substep(list(DIMS), U, ch, 0, k // 2, k % 2).updates
-    t = time.perf_counter() - t0
-    return {"value": updates / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "the first four heat-bath substeps (mu = 0, 1; both parities: %d link updates) of the %s "
-                      "beta=2.6 hot-start lattice, plain FP64 C, single thread; %.1f s"
-                      % (updates, "x".join(map(str, DIMS)), t)}
+    for k in range(nsub):
+        updates += oracle.substep(list(DIMS), U, ch, k // 8, (k // 2) % 4, k % 2).updates
+    return updates, time.perf_counter() - t0
+
+
+def cpu_baseline():
+    """The oracle as it stands (plain FP64 C) on the same 64^4 lattice: its
+    OpenMP build over every host core on two sweeps (sixteen substeps), and
+    the serial build on one core on the first four substeps (half a sweep)."""
+    import oracle
+    from oracle import build as oracle_build
+    oracle_build.build_all()
+    with oracle.parallel():
+        cores = oracle.threads()
+        upd_all, t_all = _oracle_substeps(16)
+    upd_one, t_one = _oracle_substeps(4)
+    lat = "x".join(map(str, DIMS))
+    return {"value": upd_all / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "two heat-bath sweeps (sixteen substeps, %d link updates) of the %s beta=2.6 hot-start "
+                      "lattice, the plain FP64 C oracle built with OpenMP (the sites of each substep shared "
+                      "among %d threads, one per host core); %.1f s" % (upd_all, lat, cores, t_all),
+            "single_core": {"value": upd_one / t_one, "unit": UNIT, "cores": 1,
+                            "sample": "the first four substeps (%d link updates), serial build; %.1f s"
+                                      % (upd_one, t_one)}}
 
 
 def run_gpu(args):
@@ -352,10 +422,10 @@ def run_gpu_on_stream(args):
     if rank == 0 or ws == 1:
         su2_build.build()
     barrier()
-    from paper_1010_4834_gb300 import Batch, Lattice, inputs, kernel_launches
+    from paper_1010_4834_gb300 import Batch, Lattice, inputs, kernel_launches, probe_fma
 
     V = volume(DIMS)
-    lat = Lattice(DIMS, BETA, seed=1 + rank, start="hot", prec="f32")
+    lat = Lattice(DIMS, BETA, seed=1 + rank, start="hot", prec=PREC)
     hist = np.empty((SWEEPS, 4))
     for _ in range(args.warmup):
         step(lat, hist)
@@ -384,7 +454,7 @@ def run_gpu_on_stream(args):
     # roofline of the heat-bath substep (FP32: 8 links of 16 B per update)
     t_launch, n_launch, t_isolated = substep_launch_seconds(torch, lat)
     upd_launch = V // 2
-    alg_bytes = 8 * 16 * upd_launch
+    alg_bytes = 8 * {"f32": 16, "f64": 32, "f16q": 8}[PREC] * upd_launch
     peaks, peak_kind = measured_peaks()
     achieved = alg_bytes / t_launch / 1e9
     roofline = {"bound": "hbm", "kernel": "k_heatbath<F32>", "achieved": round(achieved, 1),
@@ -481,13 +551,25 @@ def run_gpu_on_stream(args):
                                    "kernel on one site-major array (element 4 s + mu), the paper's layout"}
         lat.close()
         del lat
+        fp64_peak = probe_fma("f64")
+        extra["fma_peaks"] = {"f64": fp64_peak, "f32": probe_fma("f32"), "unit": "FLOP/s",
+                              "what": "su2_probe_fma: eight independent FMA chains per thread over a full grid"}
         for prec, n in (("f64", 4), ("f16q", 20)):
             l2 = Lattice(DIMS, BETA, seed=1, start="hot", prec=prec)
             l2.sweep(2)
             extra[prec] = {"value": n * 4 * V / timed_sweeps(torch, l2, n, reps=2), "unit": UNIT,
                            "what": "%s 64^4 heat-bath sweeps alone, %d sweeps" % (prec, n)}
+            if prec == "f64":
+                extra[prec]["roofline"] = f64_roofline(extra[prec]["value"], fp64_peak)
+            else:
+                g = extra[prec]["value"] * 64 / 1e9          # 8 links of 8 B per update
+                extra[prec]["achieved_gbs"] = round(g, 1)
+                extra[prec]["frac"] = round(g / peaks["hbm_gbs"], 4)
             l2.close()
         extra["configs"] = small_configs(torch)
+        c1 = extra["configs"]["values"]["8^4_f64_cold_100sweeps_measured"]
+        extra["configs"]["8^4_f64_roofline"] = f64_roofline(c1, fp64_peak)
+        extra["static_potential"] = static_potential_run()
         betas = inputs.batch_betas(len(BATCH_SHAPES), seed=1)
         b = Batch(BATCH_SHAPES, betas, seed=1, start="hot", prec="f32")
         groups = b.tune(4)
@@ -500,7 +582,10 @@ def run_gpu_on_stream(args):
         torch.cuda.synchronize()
         tb = a.elapsed_time(e) / 1e3
         vb = sum(volume(d) for d in BATCH_SHAPES)
+        gb = 200 * 4 * vb * 128 / tb / 1e9
         extra["batched"] = {"value": 200 * 4 * vb / tb, "unit": UNIT,
+                            "achieved_gbs": round(gb, 1), "frac": round(gb / peaks["hbm_gbs"], 4),
+                            "bytes_per_update": 128,
                             "what": "64 lattices (16 each of 8^4, 12^4, 16^4, 24^3x6), beta ~ U[2.0, 2.8], "
                                     "FP32, 200 sweeps in one persistent cooperative launch (CUDA graph)",
                             "ms_per_sweep": tb / 200 * 1e3, "groups": groups,
@@ -534,28 +619,31 @@ def run_reference(args):
         return
     import oracle
     from oracle import build as oracle_build
-    oracle_build.build()
-    ch = oracle.chain(BETA, seed=1)
-    U = oracle.init_hot(list(DIMS), ch)
-    k = 0
-    for _ in range(args.warmup):
-        oracle.substep(list(DIMS), U, ch, k // 8, (k // 2) % 4, k % 2)
-        k += 1
-    t0 = time.perf_counter()
-    updates = 0
-    for _ in range(args.steps):
-        st = oracle.substep(list(DIMS), U, ch, k // 8, (k // 2) % 4, k % 2)
-        updates += st.updates
-        k += 1
-    t = time.perf_counter() - t0
+    oracle_build.build_all()
+    with oracle.parallel():
+        cores = oracle.threads()
+        ch = oracle.chain(BETA, seed=1)
+        U = oracle.init_hot(list(DIMS), ch)
+        k = 0
+        for _ in range(args.warmup):
+            oracle.substep(list(DIMS), U, ch, k // 8, (k // 2) % 4, k % 2)
+            k += 1
+        t0 = time.perf_counter()
+        updates = 0
+        for _ in range(args.steps):
+            st = oracle.substep(list(DIMS), U, ch, k // 8, (k // 2) % 4, k % 2)
+            updates += st.updates
+            k += 1
+        t = time.perf_counter() - t0
     value = updates / t
     sample = ("each step one heat-bath substep (%d link updates) of the %s beta=2.6 hot-start lattice, "
-              "plain FP64 C oracle, single thread" % (volume(DIMS) // 2, "x".join(map(str, DIMS))))
+              "plain FP64 C oracle built with OpenMP over %d host cores"
+              % (volume(DIMS) // 2, "x".join(map(str, DIMS)), cores))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (hot start from seed)",
             "config": config(ws), "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -571,14 +659,18 @@ def main():
     ap.add_argument("--extent", type=int, default=None,
                     help="hypercubic extent override (small profiling cases only; not a bench line)")
     ap.add_argument("--sweeps", type=int, default=None, help="sweeps per step override (profiling only)")
+    ap.add_argument("--prec", choices=["f32", "f64", "f16q"], default="f32",
+                    help="link precision override (profiling only; not a bench line)")
     args = ap.parse_args()
     global DIMS, SWEEPS, WORKLOAD
     if args.extent:
         DIMS = (args.extent,) * 4
     if args.sweeps:
         SWEEPS = args.sweeps
-    if args.extent or args.sweeps:
-        WORKLOAD = "profiling case %s, %d sweeps per step" % ("x".join(map(str, DIMS)), SWEEPS)
+    global PREC
+    PREC = args.prec
+    if args.extent or args.sweeps or PREC != "f32":
+        WORKLOAD = "profiling case %s %s, %d sweeps per step" % ("x".join(map(str, DIMS)), PREC, SWEEPS)
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

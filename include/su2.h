@@ -217,9 +217,11 @@ int su2_plaquette(su2_lattice* h, double out[3]);
  * (one partial per block, at most 4096 blocks; SU2_EINVAL if a device would
  * need more).  The call allocates nothing.  The first call on each device
  * looks the array's address up with that device current; make it before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * race, so serialise them.  `cuda_stream` NULL is the legacy default stream.
- * Synchronises the stream.
+ * stream capture.  The address is kept for the life of the process: after a
+ * cudaDeviceReset of that device it is stale, and the entry point must not
+ * be called on that device again.  All calls share the array: calls that
+ * overlap on the GPU race, so serialise them.  `cuda_stream` NULL is the
+ * legacy default stream.  Synchronises the stream.
  */
 int su2_plaquette_static(const void* links, const int dims[4], int prec, double out[3], void* cuda_stream);
 
@@ -277,6 +279,18 @@ int su2_get_sites(su2_lattice* h, int64_t first, int64_t count, double* host);
  */
 int su2_kernel_launches(uint64_t* n);
 
+/*
+ * The paper has no counterpart to this entry point: a measurement helper.
+ * *flops_per_s receives this device's fused multiply-add throughput in
+ * prec SU2_F64 or SU2_F32 (2 flops per FMA), from a probe kernel of `iters`
+ * >= 1 rounds of eight independent FMA chains per thread over a grid that
+ * fills every SM, timed with CUDA events after a warm-up launch.  It is the
+ * denominator of the rooflines of arithmetic-bound kernels (the FP64 heat
+ * bath, the Wilson loops).  Allocates and frees a small output buffer and a
+ * stream; synchronises.  SU2_EINVAL for other precisions or iters < 1.
+ */
+int su2_probe_fma(int prec, int iters, double* flops_per_s);
+
 /* Sweep counter: heat-bath sweeps done since the start (or as set by set_sweep_count / load). */
 int su2_sweep_count(su2_lattice* h, uint64_t* n);
 int su2_set_sweep_count(su2_lattice* h, uint64_t n);
@@ -312,7 +326,10 @@ int su2_batch_set_options(su2_batch* b, int max_tries, int sampler);
  * a time, the eight substeps of a lattice ordered by bounded barriers among
  * the group's CTAs.  Results do not depend on G (every draw is keyed by
  * lattice, sweep, site and direction).  SU2_ETIMEOUT if a barrier wait gave
- * up; the lattices are then invalid and the handle should be destroyed.
+ * up (bounded by a 1 s timer): the links of every lattice are then undefined,
+ * while the handle itself recovers -- its barriers and error flag are cleared
+ * and its sweep counter is back at its value before the call -- so the caller
+ * can reload the lattices with su2_batch_set_links and sweep again.
  */
 int su2_batch_sweep(su2_batch* b, int n);
 

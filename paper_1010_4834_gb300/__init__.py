@@ -6,4 +6,4 @@ checkerboard heat-bath sweep, over-relaxation, plaquette, Polyakov loop, APE
 smearing and Wilson loops, behind the C ABI of include/su2.h.
 """
 from ._lib import SU2Error, load as load_library  # noqa: F401
-from .lattice import Batch, Lattice, kernel_launches  # noqa: F401
+from .lattice import Batch, Lattice, kernel_launches, probe_fma  # noqa: F401

@@ -51,6 +51,7 @@ SIGNATURES = {
     "su2_sweep_measure": (_i, [_vp, _i, _dp]),
     "su2_layout_compare": (_i, [_vp, _i, _dp, C.POINTER(_u64)]),
     "su2_kernel_launches": (_i, [C.POINTER(_u64)]),
+    "su2_probe_fma": (_i, [_i, _i, _dp]),
     "su2_overrelax_sweep": (_i, [_vp, _i]),
     "su2_plaquette": (_i, [_vp, _dp]),
     "su2_plaquette_static": (_i, [_vp, _ip, _i, _dp, _vp]),

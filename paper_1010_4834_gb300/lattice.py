@@ -37,6 +37,13 @@ def kernel_launches():
     return n.value
 
 
+def probe_fma(prec="f64", iters=1 << 14):
+    """This device's FMA throughput in flop/s (su2_probe_fma)."""
+    v = C.c_double()
+    check(_lib.load().su2_probe_fma(_lib.PREC[prec], int(iters), C.byref(v)))
+    return v.value
+
+
 def required_bytes(dims, prec):
     """Device bytes a lattice of these extents and precision needs."""
     n = C.c_size_t()

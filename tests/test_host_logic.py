@@ -76,5 +76,47 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] == os.cpu_count()      # the OpenMP build, one thread per core
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
+
+
+def test_plateau_binning_independent_series():
+    # independent draws: the error is flat from the first bin size on
+    rng = np.random.default_rng(7)
+    x = rng.normal(0.0, 1.0, 64_000)
+    m, e, b, ok = ensemble.plateau_binned(x)
+    assert ok and b <= 4
+    assert 0.85 < e / (1.0 / np.sqrt(len(x))) < 1.15
+
+
+def test_plateau_binning_finds_the_autocorrelation():
+    # AR(1) with rho = 0.95: tau_int = (1 + rho) / (2 (1 - rho)) = 19.5; the
+    # error rises with the bin size until bins are several tau long, then
+    # stays at sqrt(2 tau_int) = sqrt(39) times the naive error
+    rng = np.random.default_rng(8)
+    n, rho = 256_000, 0.95
+    eps = rng.normal(0.0, 1.0, n)
+    x = np.empty(n)
+    x[0] = eps[0]
+    for i in range(1, n):
+        x[i] = rho * x[i - 1] + np.sqrt(1 - rho * rho) * eps[i]
+    m, e, b, ok = ensemble.plateau_binned(x)
+    assert ok and 32 <= b <= 1024, b
+    assert 0.8 * np.sqrt(39) < e / (1.0 / np.sqrt(n)) < 1.2 * np.sqrt(39)
+
+
+def test_plateau_binning_reports_a_series_too_short():
+    # a random walk has no finite autocorrelation time: the error grows with
+    # every bin size and no plateau is reported
+    rng = np.random.default_rng(9)
+    x = np.cumsum(rng.normal(0.0, 1.0, 20_000))
+    _, e, b, ok = ensemble.plateau_binned(x)
+    assert not ok
+    curve = ensemble.binning_curve(x)
+    assert e == max(c[1] for c in curve)
+
+
+def test_thermalisation_drops_the_first_fifth():
+    h = np.arange(100.0)[:, None] * np.ones((1, 4))
+    assert ensemble.thermalised(h)[0, 0] == 20.0 and len(ensemble.thermalised(h)) == 80

@@ -44,3 +44,26 @@ def test_weighted_fit_uses_the_errors():
     err_bad[-1] = 1e3                        # the outlier carries no weight
     (a, b, s), _ = potential.fit_potential(R, V_bad, err_bad)
     np.testing.assert_allclose([a, b, s], [0.5, -0.3, 0.05], atol=1e-6)
+
+
+def test_ensemble_analysis_recovers_the_string_tension():
+    # synthetic ensemble: W(R,T) = c exp(-T V(R)) + excited state, with
+    # independent noise per configuration; the plateau rule must skip the
+    # small T where the excited state still shows, and the jackknife fit must
+    # find sigma within its error
+    A, B, s = 0.55, -0.27, 0.041
+    R = np.arange(1, 8)
+    T = np.arange(1, 9)
+    V = A + B / R + s * R
+    W = (0.9 * np.exp(-np.outer(V, T)) + 0.1 * np.exp(-np.outer(V + 0.8, T)))
+    rng = np.random.default_rng(4)
+    samples = W[None] * (1 + 2e-3 * rng.standard_normal((200,) + W.shape))
+    res = potential.static_potential(samples)
+    assert res["T_plateau"].min() >= 2                 # T = 1 still carries the excited state
+    assert np.all(np.diff(res["V"]) > 0)
+    assert abs(res["sigma_a2"] - s) < 4 * res["sigma_a2_err"] + 2e-3
+    assert 0 < res["sigma_a2_err"] < 0.01
+    # the jackknife error of a plain mean is the standard error
+    x = rng.standard_normal(400)
+    m, e, _ = potential.jackknife(x[:, None], lambda v: v[0])
+    assert abs(m - x.mean()) < 1e-12 and abs(e - x.std(ddof=1) / 20) < 1e-12
