@@ -235,34 +235,65 @@ def timed_sweeps(torch, lat, n, reps=3):
     return best
 
 
-def substep_launch_seconds(torch, lat, sweeps=4):
-    """Average duration of one heat-bath substep launch: one CUDA-event pair
-    around 8 * sweeps substeps launched back to back on the lattice's stream
-    (the way a sweep runs them), and, for comparison, the mean of the same
-    launches each bracketed by its own events with the stream idle between
-    them (which adds the launch latency to every launch)."""
+def launch_seconds(torch, lat, kind, sweeps=4):
+    """Average duration of one heat-bath launch of `kind` ("substep" or
+    "pair"): one CUDA-event pair around the launches of `sweeps` sweeps
+    issued back to back on the lattice's stream (the way a sweep runs them),
+    and, for comparison, the mean of the same launches each bracketed by its
+    own events with the stream idle between them (which adds the launch
+    latency to every launch)."""
+    def one(mu, p, sw):
+        if kind == "pair":
+            lat.pair(mu, sw)
+        else:
+            lat.substep(mu, p, sw)
+    parities = (0,) if kind == "pair" else (0, 1)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for sw in range(sweeps):
         for mu in range(4):
-            for p in range(2):
-                lat.substep(mu, p, 1000 + sw)
+            for p in parities:
+                one(mu, p, 1000 + sw)
     b.record()
     torch.cuda.synchronize()
-    n = 8 * sweeps
+    n = 4 * len(parities) * sweeps
     back_to_back = a.elapsed_time(b) / 1e3 / n
     times = []
     for sw in range(sweeps):
         for mu in range(4):
-            for p in range(2):
+            for p in parities:
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record()
-                lat.substep(mu, p, 2000 + sw)
+                one(mu, p, 2000 + sw)
                 b.record()
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(b) / 1e3)
     return back_to_back, n, statistics.mean(times)
+
+
+def heatbath_roofline(torch, lat, kind, peaks, peak_kind):
+    """The heat-bath kernel the sweeps run, against the measured copy peak.
+    Algorithmic bytes per update: a substep reads the 3.5 V distinct links its
+    V/2 staples need and writes V/2 (8 link transfers per update); a fused
+    parity pair reads 3.5 V and writes V for V updates (4.5 transfers)."""
+    V = volume(DIMS)
+    lb = {"f32": 16, "f64": 32, "f16q": 8}[PREC]
+    t_launch, n_launch, t_isolated = launch_seconds(torch, lat, kind)
+    if kind == "pair":
+        upd_launch, per_update, name = V, 4.5 * lb, "k_heatbath_pair<F32>"
+    else:
+        upd_launch, per_update, name = V // 2, 8 * lb, "k_heatbath<F32>"
+    alg_bytes = int(per_update * upd_launch)
+    achieved = alg_bytes / t_launch / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1),
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "peak_kind": peak_kind, "traffic": profiled_traffic(kind, upd_launch),
+            "algorithmic_bytes_per_update": per_update,
+            "algorithmic_bytes_per_launch": alg_bytes, "launch_us": round(t_launch * 1e6, 2),
+            "launches_timed": n_launch, "timing": "one event pair around %d back-to-back launches" % n_launch,
+            "launch_us_isolated": round(t_isolated * 1e6, 2),
+            "updates_per_s_in_kernel": upd_launch / t_launch}
 
 
 def reduce_over_ranks(dist, elapsed, launches, device):
@@ -288,10 +319,11 @@ def _code_only(text, python=False):
 
 
 def source_sha():
-    """Hash of the heat-bath kernel's sources (code only) and build flags."""
+    """Hash of the heat-bath kernels' sources (code only) and build flags."""
     h = hashlib.sha256()
     pkg = os.path.join(ROOT, "paper_1010_4834_gb300")
     for f in (os.path.join(pkg, "csrc", "su2_device.cuh"), os.path.join(pkg, "csrc", "su2_heatbath.cu"),
+              os.path.join(pkg, "csrc", "su2_hb_link.cuh"), os.path.join(pkg, "csrc", "su2_pair.cu"),
               os.path.join(pkg, "csrc", "su2_kernel_util.cuh"), os.path.join(pkg, "csrc", "su2_internal.h"),
               os.path.join(pkg, "build.py")):
         with open(f, encoding="utf-8") as fh:
@@ -299,17 +331,23 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(updates_per_launch):
-    """DRAM bytes per heat-bath launch from the committed ncu summary, scaled
-    by updates; None if the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "hb_substep_f32.md")
+def _profile_values(name):
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
-        return None
+        return {}
     vals = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
+    return vals
+
+
+def profiled_traffic(kind, updates_per_launch):
+    """DRAM bytes per heat-bath launch ("substep" or "pair") from the
+    committed ncu summary, scaled by updates; None if the kernel source
+    changed since the capture."""
+    vals = _profile_values("hb_pair_f32.md" if kind == "pair" else "hb_substep_f32.md")
     if vals.get("source_sha") != source_sha():
         return None
     try:
@@ -322,14 +360,7 @@ def profiled_f64_flops():
     """FP64 flops per heat-bath link update (2 DFMA + DMUL + DADD thread
     instructions, from the committed ncu summary of an FP64 substep), or None
     if the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "hb_substep_f64.md")
-    if not os.path.exists(path):
-        return None
-    vals = {}
-    for line in open(path):
-        if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
+    vals = _profile_values("hb_substep_f64.md")
     if vals.get("source_sha") != source_sha():
         return None
     try:
@@ -451,19 +482,12 @@ def run_gpu_on_stream(args):
     value = ws * updates_per_step * args.steps / elapsed
     plaq_last = float(hist[-1, 0])
 
-    # roofline of the heat-bath substep (FP32: 8 links of 16 B per update)
-    t_launch, n_launch, t_isolated = substep_launch_seconds(torch, lat)
-    upd_launch = V // 2
-    alg_bytes = 8 * {"f32": 16, "f64": 32, "f16q": 8}[PREC] * upd_launch
+    # roofline of the heat-bath kernel the sweeps run (the substep kernel),
+    # with the fused parity pair's beside it
     peaks, peak_kind = measured_peaks()
-    achieved = alg_bytes / t_launch / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_heatbath<F32>", "achieved": round(achieved, 1),
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                "peak_kind": peak_kind, "traffic": profiled_traffic(upd_launch),
-                "algorithmic_bytes_per_launch": alg_bytes, "launch_us": round(t_launch * 1e6, 2),
-                "launches_timed": n_launch, "timing": "one event pair around %d back-to-back launches" % n_launch,
-                "launch_us_isolated": round(t_isolated * 1e6, 2),
-                "updates_per_s_in_kernel": upd_launch / t_launch}
+    roofline = heatbath_roofline(torch, lat, "substep", peaks, peak_kind)
+    if PREC != "f64":
+        roofline["pair_kernel"] = heatbath_roofline(torch, lat, "pair", peaks, peak_kind)
 
     # end to end through the public API: every step starts from the
     # configuration in pinned host memory (2.15 GB canonical FP64), which the

@@ -77,6 +77,11 @@ extern "C" {
 #define SU2_SAMPLER_KP 0     /* Kennedy-Pendleton (default)                   */
 #define SU2_SAMPLER_CREUTZ 1 /* Creutz, the method the paper cites            */
 
+/* heat-bath sweep schedule (su2_set_schedule) */
+#define SU2_SCHED_AUTO 0    /* the library's choice: substeps (the faster on GB300)         */
+#define SU2_SCHED_SUBSTEP 1 /* eight substep launches per sweep                           */
+#define SU2_SCHED_PAIR 2    /* four fused parity-pair launches per sweep (FP32, F16Q)     */
+
 typedef struct su2_lattice su2_lattice;
 typedef struct su2_batch su2_batch;
 
@@ -128,6 +133,36 @@ int su2_set_options(su2_lattice* h, int max_tries, int sampler);
 
 /* Change beta (>= 0) for subsequent sweeps. */
 int su2_set_beta(su2_lattice* h, double beta);
+
+/*
+ * How heat-bath sweeps are launched; the links they leave are the same
+ * either way (every draw is keyed by sweep, site and direction, and the
+ * links of one (direction, parity) class are independent).
+ * SU2_SCHED_SUBSTEP: eight launches per sweep, one per (direction, parity)
+ * substep (Section 4's order).  SU2_SCHED_PAIR: four launches, each running
+ * the two parities of one direction as a wavefront over time slices so that
+ * the links the pair shares are re-read from L2 instead of device memory
+ * (parity 1 of slice t starts once parity 0 of slices t-1, t, t+1 is final);
+ * FP32 and F16Q only (SU2_EINVAL for FP64).  SU2_SCHED_AUTO (the default)
+ * runs substeps: measured on GB300 the pair is slower at every lattice size
+ * (64^4 FP32: about 500 us per pair launch against 375 us for its two
+ * substeps), because the substep kernel is bound by memory latency and
+ * instruction issue rather than by the traffic the pair saves.
+ * The pair's dependency waits are bounded; if one gives up, the next call
+ * that synchronises returns SU2_ETIMEOUT and the links are undefined.
+ * Drops the cached sweep graphs.
+ */
+int su2_set_schedule(su2_lattice* h, int schedule);
+
+/*
+ * n in 0..16 over-relaxation sweeps (Section 2, Eq. 10; as
+ * su2_overrelax_sweep) before every heat-bath sweep of su2_heatbath_sweep
+ * and su2_sweep_measure, the usual way to shorten autocorrelation times.
+ * They come first because over-relaxation keeps the total action but not
+ * its spatial / space-time split, which su2_sweep_measure takes from the
+ * heat bath's own staples.  Default 0.  Drops the cached sweep graphs.
+ */
+int su2_set_overrelax(su2_lattice* h, int n);
 
 /*
  * n >= 0 heat-bath sweeps.  One sweep = for mu = 0..3, for parity = 0, 1:
@@ -187,6 +222,15 @@ int su2_layout_compare(su2_lattice* h, int sweeps, double ms[3], uint64_t* misma
 int su2_heatbath_substep(su2_lattice* h, int mu, int parity, uint32_t sweep);
 
 /*
+ * Both substeps of direction mu (parity 0, then parity 1) with Philox sweep
+ * index `sweep`, as one fused launch (see su2_set_schedule); leaves the links
+ * that su2_heatbath_substep(mu, 0, sweep) then (mu, 1, sweep) leave.  FP32
+ * and F16Q only (SU2_EINVAL for FP64).  Does not change the sweep counter.
+ * Exposed for parity tests and custom schedules.
+ */
+int su2_heatbath_pair(su2_lattice* h, int mu, uint32_t sweep);
+
+/*
  * n >= 0 over-relaxation sweeps, U -> W U^dagger W with W = Sigma/|Sigma|
  * (Section 2, Eq. 10, read for the staple orientation of Eq. 11).  Same
  * direction/parity order as the heat bath.  Deterministic; the sweep counter
@@ -224,6 +268,34 @@ int su2_plaquette(su2_lattice* h, double out[3]);
  * legacy default stream.  Synchronises the stream.
  */
 int su2_plaquette_static(const void* links, const int dims[4], int prec, double out[3], void* cuda_stream);
+
+/*
+ * Support for splitting one lattice into time slabs over several GPUs
+ * (Section 4's multi-GPU decomposition; the driver is
+ * paper_1010_4834_gb300/tslab.py).  A slab is a lattice of its own whose
+ * first and last time slices are copies of the neighbouring slabs' boundary
+ * slices (ghosts).
+ *
+ * su2_set_site_offset: the Philox counter of local site s uses site word
+ * s + site0 (mod 2^32) in every later draw (heat bath, hot start), so that a
+ * slab draws the numbers of the whole lattice: site0 = (global time of local
+ * slice 0) x N0 N1 N2.  Default 0.  Drops the cached sweep graphs.
+ *
+ * su2_plaquette_slices: as su2_plaquette, over the plaquettes whose base site
+ * lies in time slices [t_first, t_first + t_count) only (means over those
+ * 6 N0 N1 N2 t_count plaquettes).  SU2_EINVAL for a range outside the
+ * lattice.  Synchronises.
+ *
+ * su2_time_lines: for every spatial site xs (index x0 + N0 (x1 + N1 x2)) the
+ * product U_3(xs, t_first) U_3(xs, t_first + 1) ... of the time links of
+ * slices [t_first, t_first + t_count), in FP64, to out[4 xs .. 4 xs + 3]
+ * (caller-owned host memory of 4 N0 N1 N2 doubles); the slabs' lines,
+ * multiplied in time order, give the Polyakov loop (Eqs. 14-15).
+ * SU2_EINVAL for a range outside the lattice.  Synchronises.
+ */
+int su2_set_site_offset(su2_lattice* h, uint32_t site0);
+int su2_plaquette_slices(su2_lattice* h, int t_first, int t_count, double out[3]);
+int su2_time_lines(su2_lattice* h, int t_first, int t_count, double* out);
 
 /*
  * Signed Polyakov loop (Section 2, Eqs. 14-15): mean over the N0 N1 N2
@@ -332,6 +404,13 @@ int su2_batch_set_options(su2_batch* b, int max_tries, int sampler);
  * can reload the lattices with su2_batch_set_links and sweep again.
  */
 int su2_batch_sweep(su2_batch* b, int n);
+
+/*
+ * n in 0..16 over-relaxation sweeps (Section 2, Eq. 10) of every lattice
+ * before each of its heat-bath sweeps, inside the same persistent launch
+ * (as su2_set_overrelax for one lattice).  Default 0.
+ */
+int su2_batch_set_overrelax(su2_batch* b, int n);
 
 /*
  * The schedule's group count G (1 <= G <= min(lattices, co-resident CTAs)).

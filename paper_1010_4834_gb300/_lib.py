@@ -16,6 +16,8 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, 1, 2, 3, 4, 5
 COLD, HOT = 0, 1
 F64, F32, F16Q = 0, 1, 2
 SAMPLER_KP, SAMPLER_CREUTZ = 0, 1
+SCHED_AUTO, SCHED_SUBSTEP, SCHED_PAIR = 0, 1, 2
+SCHEDULE = {"auto": SCHED_AUTO, "substep": SCHED_SUBSTEP, "pair": SCHED_PAIR}
 
 PREC = {"f64": F64, "f32": F32, "f16q": F16Q, F64: F64, F32: F32, F16Q: F16Q}
 START = {"cold": COLD, "hot": HOT, COLD: COLD, HOT: HOT}
@@ -45,8 +47,11 @@ SIGNATURES = {
     "su2_set_stream": (_i, [_vp, _vp]),
     "su2_set_options": (_i, [_vp, _i, _i]),
     "su2_set_beta": (_i, [_vp, _d]),
+    "su2_set_schedule": (_i, [_vp, _i]),
+    "su2_set_overrelax": (_i, [_vp, _i]),
     "su2_heatbath_sweep": (_i, [_vp, _i]),
     "su2_heatbath_substep": (_i, [_vp, _i, _i, _u32]),
+    "su2_heatbath_pair": (_i, [_vp, _i, _u32]),
     "su2_restart": (_i, [_vp, _i]),
     "su2_sweep_measure": (_i, [_vp, _i, _dp]),
     "su2_layout_compare": (_i, [_vp, _i, _dp, C.POINTER(_u64)]),
@@ -56,6 +61,9 @@ SIGNATURES = {
     "su2_plaquette": (_i, [_vp, _dp]),
     "su2_plaquette_static": (_i, [_vp, _ip, _i, _dp, _vp]),
     "su2_polyakov": (_i, [_vp, _dp]),
+    "su2_set_site_offset": (_i, [_vp, _u32]),
+    "su2_plaquette_slices": (_i, [_vp, _i, _i, _dp]),
+    "su2_time_lines": (_i, [_vp, _i, _i, _dp]),
     "su2_ape_smear": (_i, [_vp, _d, _i]),
     "su2_wilson_loops": (_i, [_vp, _i, _i, _i, _dp]),
     "su2_get_links": (_i, [_vp, _dp]),
@@ -68,6 +76,7 @@ SIGNATURES = {
     "su2_batch_init": (_i, [_pp, _i, _ip, _dp, _u64, _i, _i, _vp]),
     "su2_batch_destroy": (_i, [_vp]),
     "su2_batch_set_options": (_i, [_vp, _i, _i]),
+    "su2_batch_set_overrelax": (_i, [_vp, _i]),
     "su2_batch_sweep": (_i, [_vp, _i]),
     "su2_batch_set_groups": (_i, [_vp, _i]),
     "su2_batch_groups": (_i, [_vp, _ip]),

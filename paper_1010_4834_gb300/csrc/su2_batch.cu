@@ -26,6 +26,7 @@
 
 #include "su2.h"
 #include "su2_capi_util.h"
+#include "su2_hb_link.cuh"
 #include "su2_internal.h"
 
 using namespace su2;
@@ -118,7 +119,7 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
     if (h >= vh) continue;
     const Site x = site_from_half(g, (uint32_t)h, p);
     const Quat<R> sig = staple<P, MU, 0xF, false>(L, g, x, h, p);
-    const uint32_t site = site_index(g, x);
+    const uint32_t site = philox_site(g, x);
     const uint4 ctr = make_uint4(site, tag, sweep, 0u);
     const R k2 = qdot(sig, sig);
     const R invk = M::rsqrt(k2);
@@ -162,11 +163,20 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
   if (threadIdx.x == 0) *qn = 0;
 }
 
+// One over-relaxation substep (MU, p) of one lattice by the CTAs of a group.
+template <int P, int MU, int PAR>
+__device__ __forceinline__ void batch_or_substep(const Links<P, true>& L, const Geom& g, int rank, int cpg) {
+  const int vh = (int)g.vh;
+  for (int h = rank * kBatchThreads + (int)threadIdx.x; h < vh; h += cpg * kBatchThreads)
+    or_link<P, MU, PAR, false>(L, g, h);
+}
+
+// Four blocks of 256 per SM (64 registers a thread) for FP32 / F16Q, two for FP64.
 template <int P>
-__global__ void __launch_bounds__(kBatchThreads)
+__global__ void __launch_bounds__(kBatchThreads, P == kF64 ? 2 : 4)
     k_batch_groups(const BatchLattice* __restrict__ desc, const int* __restrict__ order,
-                   const int2* __restrict__ plan, int groups, int cpg, int nsweeps, const uint32_t* sweep_base,
-                   const __grid_constant__ HBParams hp, GroupBarrier* bars, BatchCtl* ctl,
+                   const int2* __restrict__ plan, int groups, int cpg, int nsweeps, int nor,
+                   const uint32_t* sweep_base, const __grid_constant__ HBParams hp, GroupBarrier* bars, BatchCtl* ctl,
                    unsigned long long timeout_ns) {
   using R = typename Real<P>::T;
   __shared__ BDeferred<R> queue[kBatchQueue];
@@ -200,13 +210,36 @@ __global__ void __launch_bounds__(kBatchThreads)
   // stay in L2 through its sweeps (interleaving the group's lattices between
   // barriers halves the barriers but spills the working set: 32.5 against
   // 35.5 G updates/s for the 64-lattice batch at 32 groups)
+  // `nor` over-relaxation sweeps precede each heat-bath sweep
+  auto or_substep = [&](int l, int mu, int p) {
+    const Geom g = desc[l].g;
+    Links<P, true> L;
+    L.set(desc[l].links, g.vh);
+    switch (2 * mu + p) {
+      case 0: batch_or_substep<P, 0, 0>(L, g, rank, cpg); break;
+      case 1: batch_or_substep<P, 0, 1>(L, g, rank, cpg); break;
+      case 2: batch_or_substep<P, 1, 0>(L, g, rank, cpg); break;
+      case 3: batch_or_substep<P, 1, 1>(L, g, rank, cpg); break;
+      case 4: batch_or_substep<P, 2, 0>(L, g, rank, cpg); break;
+      case 5: batch_or_substep<P, 2, 1>(L, g, rank, cpg); break;
+      case 6: batch_or_substep<P, 3, 0>(L, g, rank, cpg); break;
+      default: batch_or_substep<P, 3, 1>(L, g, rank, cpg); break;
+    }
+  };
   for (int li = 0; li < pl.y; ++li)
-    for (int sw = 0; sw < nsweeps; ++sw)
+    for (int sw = 0; sw < nsweeps; ++sw) {
+      for (int k = 0; k < nor; ++k)
+        for (int mu = 0; mu < 4; ++mu)
+          for (int p = 0; p < 2; ++p) {
+            or_substep(order[pl.x + li], mu, p);
+            if (!group_barrier(bars + group, (unsigned)cpg, ctl, timeout_ns)) return;
+          }
       for (int mu = 0; mu < 4; ++mu)
         for (int p = 0; p < 2; ++p) {
           substep(order[pl.x + li], sweep0 + (uint32_t)sw, mu, p);
           if (!group_barrier(bars + group, (unsigned)cpg, ctl, timeout_ns)) return;
         }
+    }
 }
 
 }  // namespace su2
@@ -241,6 +274,9 @@ struct su2_batch {
   int grid;    // co-resident CTAs
   int groups;  // current G
   unsigned long long timeout_ns;
+  int nor;                   // over-relaxation sweeps before each heat-bath sweep
+  unsigned int fault_extra;  // injected missing barrier arrivals (0: none)
+  bool fault_once;           // the injected fault is withdrawn after its first timeout
 };
 
 namespace {
@@ -354,20 +390,41 @@ cudaError_t launch_groups(const su2_batch* b, const BatchLattice* d_desc, int n,
   const uint32_t* sw = b->d_sweep;
   cudaError_t e;
   switch (b->prec) {
-    case kF64: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF64>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
-    case kF32: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF32>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
-    default: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF16Q>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
+    case kF64: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF64>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
+    case kF32: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF32>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
+    default: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF16Q>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
   }
   if (e == cudaSuccess) count_launches(1);
   return e;
 }
 
-int check_ctl(su2_batch* b) {
+// After a batched sweep: SU2_ETIMEOUT if a barrier wait gave up.  The handle
+// then recovers for the next call: the error flag and every group barrier
+// are cleared and the sweep counters (host and device) go back to their
+// values before the call (`sweep_before`); the links are left as the
+// aborted kernel left them, which is undefined.
+int check_ctl(su2_batch* b, uint64_t sweep_before) {
   int err = 0;
   SU2_CU(cudaMemcpyAsync(&err, &b->d_ctl->err, sizeof err, cudaMemcpyDeviceToHost, b->stream));
   SU2_CU(cudaStreamSynchronize(b->stream));
-  if (err) return fail(SU2_ETIMEOUT, "a group barrier of the batched sweep timed out; lattice contents are invalid");
-  return SU2_OK;
+  if (!err) return SU2_OK;
+  if (b->fault_once) {
+    b->fault_extra = 0;
+    b->fault_once = false;
+    b->timeout_ns = 1000000000ull;
+    drop_graph(b);  // the captured launch carries the short test timeout
+  }
+  BatchCtl ctl;
+  std::memset(&ctl, 0, sizeof ctl);
+  ctl.extra = b->fault_extra;
+  const uint32_t sw = (uint32_t)sweep_before;
+  SU2_CU(cudaMemcpyAsync(b->d_ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, b->stream));
+  SU2_CU(cudaMemsetAsync(b->d_bars, 0, kMaxGroups * sizeof(GroupBarrier), b->stream));
+  SU2_CU(cudaMemcpyAsync(b->d_sweep, &sw, sizeof sw, cudaMemcpyHostToDevice, b->stream));
+  SU2_CU(cudaStreamSynchronize(b->stream));
+  b->sweep = sweep_before;
+  return fail(SU2_ETIMEOUT, "a group barrier of the batched sweep timed out; the links of every lattice are "
+                            "undefined (reload them with su2_batch_set_links)");
 }
 
 }  // namespace
@@ -450,10 +507,13 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   std::memset(&ctl, 0, sizeof ctl);
   // Fault injection for the timeout path, host-side switch: every barrier
   // then waits for one arrival that never comes and every wait runs out.
+  // SU2_FAULT=barrier_once: the same for the first batched sweep only (the
+  // recovery test).
   const char* fault = std::getenv("SU2_FAULT");
-  if (fault && std::strcmp(fault, "barrier") == 0) {
-    ctl.extra = 1;
+  if (fault && (std::strcmp(fault, "barrier") == 0 || std::strcmp(fault, "barrier_once") == 0)) {
+    ctl.extra = b->fault_extra = 1;
     b->timeout_ns = 20000000ull;
+    b->fault_once = std::strcmp(fault, "barrier_once") == 0;
   }
   SU2_CU_CLEAN(cudaMemcpyAsync(b->d_ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, b->stream), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaMemsetAsync(b->d_sweep, 0, 64, b->stream), su2_batch_destroy(b));
@@ -492,6 +552,15 @@ extern "C" int su2_batch_set_options(su2_batch* b, int max_tries, int sampler) {
   if (sampler != SU2_SAMPLER_KP && sampler != SU2_SAMPLER_CREUTZ) return fail(SU2_EINVAL, "unknown sampler %d", sampler);
   b->max_tries = max_tries;
   b->sampler = sampler;
+  drop_graph(b);
+  return SU2_OK;
+}
+
+extern "C" int su2_batch_set_overrelax(su2_batch* b, int n) {
+  clear_error();
+  if (!b) return fail(SU2_EINVAL, "handle is NULL");
+  if (n < 0 || n > 16) return fail(SU2_EINVAL, "over-relaxation sweeps per heat-bath sweep must be in 0..16");
+  b->nor = n;
   drop_graph(b);
   return SU2_OK;
 }
@@ -539,11 +608,12 @@ extern "C" int su2_batch_sweep(su2_batch* b, int n) {
     }
     b->graph_n = n;
   }
+  const uint64_t before = b->sweep;
   SU2_CU(cudaGraphLaunch(b->graph, b->stream));
   count_launches(2);
   b->sweep += (uint64_t)n;
   // a timed-out barrier is reported by the call that ran it
-  return check_ctl(b);
+  return check_ctl(b, before);
 }
 
 extern "C" int su2_batch_tune(su2_batch* b, int sweeps, int* groups) {
@@ -595,8 +665,8 @@ extern "C" int su2_batch_tune(su2_batch* b, int sweeps, int* groups) {
       set_groups(b, original);
       return fail(SU2_ECUDA, "tuning launch failed: %s", cudaGetErrorString(e));
     }
-    int rc2 = check_ctl(b);
-    if (rc2) { cleanup(); return rc2; }
+    int rc2 = check_ctl(b, b->sweep);
+    if (rc2) { cleanup(); set_groups(b, original); return rc2; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) { best_ms = ms; best = G; }

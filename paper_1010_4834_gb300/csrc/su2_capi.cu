@@ -68,6 +68,12 @@ struct su2_lattice {
   int graph_sweeps;
   int meas_nb[3];          // blocks of the three plaquette-summing substeps
   int smeared;  // 0 none, 1 in ape[0], 2 in ape[1]
+  // sweep schedule and the fused pair's control block
+  int schedule;            // SU2_SCHED_*
+  int or_per_sweep;        // over-relaxation sweeps before each heat-bath sweep
+  PairCtl* d_pair;
+  unsigned int* d_done0;   // one count per time slice
+  bool pair_used;          // a pair launch ran since the last error check
 };
 
 namespace {
@@ -76,8 +82,9 @@ constexpr int kGraphSweeps = 8;
 constexpr int64_t kStagingSites = (int64_t)1 << 18;
 
 struct Layout {
-  size_t links, ape0, ape1, partials, counter, out, state, hist, staging, total;
+  size_t links, ape0, ape1, partials, counter, out, state, hist, pair, staging, total;
 };
+
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -94,6 +101,7 @@ Layout layout_for(const int dims[4], int prec) {
   L.out = o; o = align256(o + kScratchOut * sizeof(double));
   L.state = o; o = align256(o + 256);
   L.hist = o; o = align256(o + (size_t)kHistRing * 4 * sizeof(double));
+  L.pair = o; o = align256(o + sizeof(PairCtl) + (size_t)dims[3] * sizeof(unsigned int));
   const int64_t st = V < kStagingSites ? V : kStagingSites;
   L.staging = o; o = align256(o + (size_t)st * 16 * sizeof(double));
   L.total = o;
@@ -207,6 +215,10 @@ static int init_common(su2_lattice** out, const int dims[4], double beta, uint64
   h->d_sweep = (uint32_t*)(b + L.state);
   h->d_stats = (unsigned long long*)(b + L.state + 64);
   h->d_hist = (double*)(b + L.hist);
+  h->d_pair = (PairCtl*)(b + L.pair);
+  h->d_done0 = (unsigned int*)(b + L.pair + sizeof(PairCtl));
+  h->schedule = SU2_SCHED_AUTO;
+  h->or_per_sweep = 0;
   h->staging = (double*)(b + L.staging);
   const int64_t V = 2 * h->g.vh;
   h->staging_sites = V < kStagingSites ? V : kStagingSites;
@@ -221,6 +233,7 @@ static int init_common(su2_lattice** out, const int dims[4], double beta, uint64
   SU2_CU_CLEAN(cudaMallocHost(&h->h_out, kScratchOut * sizeof(double)), su2_destroy(h));
   SU2_CU_CLEAN(cudaMemsetAsync(b + L.counter, 0, L.out - L.counter, h->stream), su2_destroy(h));
   SU2_CU_CLEAN(cudaMemsetAsync(b + L.state, 0, 256, h->stream), su2_destroy(h));
+  SU2_CU_CLEAN(cudaMemsetAsync(b + L.pair, 0, L.staging - L.pair, h->stream), su2_destroy(h));
   SU2_CU_CLEAN(launch_init(view(h), start, philox_key(h->seed), 0u, h->stream), su2_destroy(h));
   *out = h;
   return SU2_OK;
@@ -296,37 +309,126 @@ extern "C" int su2_set_beta(su2_lattice* h, double beta) {
   return SU2_OK;
 }
 
-// One sweep's eight substeps; sweep index = *d_sweep + off.
+extern "C" int su2_set_schedule(su2_lattice* h, int schedule) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (schedule != SU2_SCHED_AUTO && schedule != SU2_SCHED_SUBSTEP && schedule != SU2_SCHED_PAIR)
+    return fail(SU2_EINVAL, "unknown schedule %d", schedule);
+  if (schedule == SU2_SCHED_PAIR && h->prec == SU2_F64)
+    return fail(SU2_EINVAL, "the fused pair schedule runs FP32 and F16Q lattices only");
+  h->schedule = schedule;
+  drop_graph(h);
+  return SU2_OK;
+}
+
+extern "C" int su2_set_overrelax(su2_lattice* h, int n) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (n < 0 || n > 16) return fail(SU2_EINVAL, "over-relaxation sweeps per heat-bath sweep must be in 0..16");
+  h->or_per_sweep = n;
+  drop_graph(h);
+  return SU2_OK;
+}
+
+// Whether heat-bath sweeps run as four fused parity pairs (su2_pair.cu)
+// rather than eight substeps.
+// SU2_SCHED_AUTO is the substep schedule: measured on GB300 the fused pair
+// is slower at every size (64^4 FP32: 495-540 us per pair against 375 us for
+// its two substeps), since the substep kernel is bound by latency and issue,
+// not by the HBM traffic the pair saves.
+static bool use_pair(const su2_lattice* h) {
+  return h->prec != SU2_F64 && h->schedule == SU2_SCHED_PAIR;
+}
+
+// Kernels one (plain or measured) sweep enqueues.
+static int kernels_per_sweep(const su2_lattice* h, bool measured) {
+  return 8 * h->or_per_sweep + (use_pair(h) ? 4 : 8) + (measured ? 1 : 0);
+}
+
+// The over-relaxation sweeps that precede each heat-bath sweep (Section 2,
+// Eq. 10; same direction and parity order).
+static cudaError_t enqueue_overrelax(su2_lattice* h, cudaStream_t st) {
+  const LatticeView v = view(h);
+  for (int k = 0; k < h->or_per_sweep; ++k)
+    for (int mu = 0; mu < 4; ++mu)
+      for (int p = 0; p < 2; ++p) {
+        cudaError_t e = launch_overrelax(v, mu, p, st);
+        if (e != cudaSuccess) return e;
+      }
+  return cudaSuccess;
+}
+
+// One sweep's eight substeps (or four fused pairs), after the handle's
+// over-relaxation sweeps; sweep index = *d_sweep + off.
 static cudaError_t enqueue_sweep(su2_lattice* h, uint32_t off, cudaStream_t st) {
   const LatticeView v = view(h);
   const HBParams hp = hb_params(h);
+  cudaError_t e = enqueue_overrelax(h, st);
+  if (e != cudaSuccess) return e;
+  if (use_pair(h)) {
+    h->pair_used = true;
+    for (int mu = 0; mu < 4; ++mu) {
+      e = launch_heatbath_pair(v, mu, h->d_sweep, off, hp, h->d_pair, h->d_done0, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   for (int mu = 0; mu < 4; ++mu)
     for (int p = 0; p < 2; ++p) {
-      cudaError_t e = launch_heatbath(v, mu, p, h->d_sweep, off, hp, nullptr, st);
+      e = launch_heatbath(v, mu, p, h->d_sweep, off, hp, nullptr, st);
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
 }
 
-// One measured sweep: the eight substeps, the odd-parity ones of mu = 1, 2, 3
-// also summing the plaquettes their links close (see k_heatbath), then the
-// Polyakov kernel, whose last block turns those block sums into the
-// plaquette, records both in row (*d_sweep mod kHistRing) of d_hist and
-// advances *d_sweep.  No host state changes, so it replays in a graph.
+// One measured sweep: the over-relaxation sweeps, the eight substeps (or
+// four pairs), the odd-parity ones of mu = 1, 2, 3 also summing the
+// plaquettes their links close (see k_heatbath), then the Polyakov kernel,
+// whose last block turns those block sums into the plaquette, records both
+// in row (*d_sweep mod kHistRing) of d_hist and advances *d_sweep.  No host
+// state changes, so it replays in a graph.  Over-relaxation keeps the total
+// action but not its spatial / space-time split, so it runs before the
+// heat bath, whose own staples give the plaquette of the final links.
 static cudaError_t enqueue_measured_sweep(su2_lattice* h, cudaStream_t st) {
   const LatticeView v = view(h);
   const HBParams hp = hb_params(h);
-  for (int mu = 0; mu < 4; ++mu)
+  cudaError_t e = enqueue_overrelax(h, st);
+  if (e != cudaSuccess) return e;
+  const bool pair = use_pair(h);
+  if (pair) h->pair_used = true;
+  for (int mu = 0; mu < 4; ++mu) {
+    double* meas = mu >= 1 ? h->scratch.partials + (size_t)(mu - 1) * kMeasStride : nullptr;
+    int* nb = meas ? &h->meas_nb[mu - 1] : nullptr;
+    if (pair) {
+      e = launch_heatbath_pair(v, mu, h->d_sweep, 0u, hp, h->d_pair, h->d_done0, st, meas, nb);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     for (int p = 0; p < 2; ++p) {
-      double* meas = (mu >= 1 && p == 1) ? h->scratch.partials + (size_t)(mu - 1) * kMeasStride : nullptr;
-      cudaError_t e = launch_heatbath(v, mu, p, h->d_sweep, 0u, hp, nullptr, st, meas, meas ? &h->meas_nb[mu - 1] : nullptr);
+      e = launch_heatbath(v, mu, p, h->d_sweep, 0u, hp, nullptr, st, p == 1 ? meas : nullptr,
+                          p == 1 ? nb : nullptr);
       if (e != cudaSuccess) return e;
     }
+  }
   SweepEpilogue ep{h->scratch.partials, {h->meas_nb[0], h->meas_nb[1], h->meas_nb[2]}, (double)(2 * v.g.vh),
                    h->d_hist, h->d_sweep};
   Scratch sp = h->scratch;
   sp.partials = h->scratch.partials + 3 * (size_t)kMeasStride;  // clear of the block sums
   return launch_polyakov(v, sp, st, &ep);
+}
+
+// SU2_ETIMEOUT if a fused-pair dependency wait gave up since the last check
+// (the stream must be synchronised); the control block is then cleared.
+static int check_pair(su2_lattice* h) {
+  if (!h->pair_used && !use_pair(h)) return SU2_OK;
+  unsigned int err = 0;
+  SU2_CU(cudaMemcpyAsync(&err, &h->d_pair->err, sizeof err, cudaMemcpyDeviceToHost, h->stream));
+  SU2_CU(cudaStreamSynchronize(h->stream));
+  h->pair_used = false;
+  if (!err) return SU2_OK;
+  SU2_CU(cudaMemsetAsync(h->d_pair, 0, sizeof(PairCtl) + (size_t)h->dims[3] * sizeof(unsigned int), h->stream));
+  SU2_CU(cudaStreamSynchronize(h->stream));
+  return fail(SU2_ETIMEOUT, "a dependency wait of the fused heat-bath sweep timed out; the links are undefined");
 }
 
 // Capture kGraphSweeps plain (measured = false) or measured sweeps.
@@ -371,7 +473,7 @@ extern "C" int su2_heatbath_sweep(su2_lattice* h, int n) {
     }
     while (left >= kGraphSweeps) {
       SU2_CU(cudaGraphLaunch(h->graph, h->stream));
-      count_launches(8 * kGraphSweeps + 1);
+      count_launches(kernels_per_sweep(h, false) * kGraphSweeps + 1);
       left -= kGraphSweeps;
     }
   }
@@ -411,7 +513,7 @@ extern "C" int su2_sweep_measure(su2_lattice* h, int n, double* hist) {
       }
       while (left >= kGraphSweeps) {
         SU2_CU(cudaGraphLaunch(h->mgraph, h->stream));
-        count_launches(9 * kGraphSweeps);
+        count_launches(kernels_per_sweep(h, true) * kGraphSweeps);
         left -= kGraphSweeps;
       }
     }
@@ -429,7 +531,7 @@ extern "C" int su2_sweep_measure(su2_lattice* h, int n, double* hist) {
   }
   h->sweep += (uint64_t)n;
   if (n) h->smeared = 0;
-  return SU2_OK;
+  return check_pair(h);
 }
 
 extern "C" int su2_layout_compare(su2_lattice* h, int sweeps, double ms[3], uint64_t* mismatch) {
@@ -520,6 +622,18 @@ extern "C" int su2_heatbath_substep(su2_lattice* h, int mu, int parity, uint32_t
   return SU2_OK;
 }
 
+extern "C" int su2_heatbath_pair(su2_lattice* h, int mu, uint32_t sweep) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  if (mu < 0 || mu > 3) return fail(SU2_EINVAL, "mu must be 0..3");
+  if (h->prec == SU2_F64) return fail(SU2_EINVAL, "the fused pair runs FP32 and F16Q lattices only");
+  DeviceGuard dg(h->device);
+  h->pair_used = true;
+  SU2_CU(launch_heatbath_pair(view(h), mu, nullptr, sweep, hb_params(h), h->d_pair, h->d_done0, h->stream));
+  h->smeared = 0;
+  return SU2_OK;
+}
+
 extern "C" int su2_overrelax_sweep(su2_lattice* h, int n) {
   clear_error();
   if (!h) return fail(SU2_EINVAL, "handle is NULL");
@@ -535,6 +649,8 @@ extern "C" int su2_overrelax_sweep(su2_lattice* h, int n) {
 static int fetch_out(su2_lattice* h, int count, double* dst) {
   SU2_CU(cudaMemcpyAsync(h->h_out, h->scratch.out, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   SU2_CU(cudaStreamSynchronize(h->stream));
+  int rc = check_pair(h);
+  if (rc) return rc;
   std::memcpy(dst, h->h_out, count * sizeof(double));
   return SU2_OK;
 }
@@ -545,6 +661,43 @@ extern "C" int su2_plaquette(su2_lattice* h, double out[3]) {
   DeviceGuard dg(h->device);
   SU2_CU(launch_plaquette(view(h), h->scratch, h->stream));
   return fetch_out(h, 3, out);
+}
+
+extern "C" int su2_plaquette_slices(su2_lattice* h, int t_first, int t_count, double out[3]) {
+  clear_error();
+  if (!h || !out) return fail(SU2_EINVAL, "NULL argument");
+  if (t_first < 0 || t_count < 1 || t_first + t_count > h->dims[3])
+    return fail(SU2_EINVAL, "time slices [%d, %d) outside 0..%d", t_first, t_first + t_count, h->dims[3]);
+  DeviceGuard dg(h->device);
+  const int64_t nsig = 2 * h->g.vh / h->dims[3];
+  SU2_CU(launch_plaquette(view(h), h->scratch, h->stream, nsig * t_first, nsig * t_count));
+  return fetch_out(h, 3, out);
+}
+
+extern "C" int su2_time_lines(su2_lattice* h, int t_first, int t_count, double* out) {
+  clear_error();
+  if (!h || !out) return fail(SU2_EINVAL, "NULL argument");
+  if (t_first < 0 || t_count < 1 || t_first + t_count > h->dims[3])
+    return fail(SU2_EINVAL, "time slices [%d, %d) outside 0..%d", t_first, t_first + t_count, h->dims[3]);
+  DeviceGuard dg(h->device);
+  const int64_t nsig = 2 * h->g.vh / h->dims[3];
+  const int64_t chunk = 4 * h->staging_sites;  // spatial sites whose 4 doubles fit the staging buffer
+  for (int64_t x0 = 0; x0 < nsig; x0 += chunk) {
+    const int64_t nx = nsig - x0 < chunk ? nsig - x0 : chunk;
+    SU2_CU(launch_time_lines(view(h), t_first, t_count, x0, nx, h->staging, h->stream));
+    SU2_CU(cudaMemcpyAsync(out + 4 * x0, h->staging, (size_t)nx * 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+  }
+  SU2_CU(cudaStreamSynchronize(h->stream));
+  return check_pair(h);
+}
+
+extern "C" int su2_set_site_offset(su2_lattice* h, uint32_t site0) {
+  clear_error();
+  if (!h) return fail(SU2_EINVAL, "handle is NULL");
+  h->g.site0 = site0;
+  drop_graph(h);
+  return SU2_OK;
 }
 
 extern "C" int su2_polyakov(su2_lattice* h, double* L) {
@@ -627,7 +780,7 @@ static int copy_sites_out(su2_lattice* h, int64_t first, int64_t count, double* 
                            cudaMemcpyDeviceToHost, h->stream));
   }
   SU2_CU(cudaStreamSynchronize(h->stream));
-  return SU2_OK;
+  return check_pair(h);
 }
 
 extern "C" int su2_get_links(su2_lattice* h, double* host) {

@@ -347,6 +347,11 @@ template <bool CP> struct Links<kF64, CP> {
     const double2 a = q[0], b = q[1];
     return qmake<double>(a.x, a.y, b.x, b.y);
   }
+  __device__ __forceinline__ Quat<double> ldcg(int cls, int i) const {
+    const double2* q = at(cls, i);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1);
+    return qmake<double>(a.x, a.y, b.x, b.y);
+  }
   __device__ __forceinline__ void st(int cls, int i, const Quat<double>& v) const {
     double2* q = at(cls, i);
     q[0] = make_double2(v.w, v.x);
@@ -389,6 +394,10 @@ template <bool CP> struct Links<kF32, CP> {
     const float4 a = *at(cls, i);
     return qmake<float>(a.x, a.y, a.z, a.w);
   }
+  __device__ __forceinline__ Quat<float> ldcg(int cls, int i) const {
+    const float4 a = __ldcg(at(cls, i));
+    return qmake<float>(a.x, a.y, a.z, a.w);
+  }
   __device__ __forceinline__ void st(int cls, int i, const Quat<float>& v) const {
     *at(cls, i) = make_float4(v.w, v.x, v.y, v.z);
   }
@@ -420,6 +429,7 @@ template <bool CP> struct Links<kF16Q, CP> {
   }
   __device__ __forceinline__ Quat<float> ld(int cls, int i) const { return unpack(__ldg(at(cls, i))); }
   __device__ __forceinline__ Quat<float> ldc(int cls, int i) const { return unpack(*at(cls, i)); }
+  __device__ __forceinline__ Quat<float> ldcg(int cls, int i) const { return unpack(__ldcg(at(cls, i))); }
   static __device__ __forceinline__ Quat<float> unpack(const uint2 a) {
     const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
     const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
@@ -446,6 +456,17 @@ template <bool CP> struct Links<kF16Q, CP> {
 template <int P, bool NC, bool CP>
 __device__ __forceinline__ Quat<typename Real<P>::T> ldl(const Links<P, CP>& L, int cls, int i) {
   return NC ? L.ld(cls, i) : L.ldc(cls, i);
+}
+
+// Loads of the staple's MU-direction links (the class of the other parity).
+// With MCG they go through L2 only (ld.global.cg): in a kernel that writes
+// that class earlier in the same launch (the fused parity pair), another
+// SM's write is visible in L2 after its release, while an L1 line read
+// before it could be stale.
+template <int P, bool NC, bool MCG, bool CP>
+__device__ __forceinline__ Quat<typename Real<P>::T> ldmu(const Links<P, CP>& L, int cls, int i) {
+  if constexpr (MCG) return L.ldcg(cls, i);
+  else return ldl<P, NC>(L, cls, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -478,6 +499,8 @@ struct Geom {
   int hst[4];       // n0h * st[d]: half-index change of a unit step in direction d >= 1
   int hwr[4];       // n0h * wr[d]: half-index change of a wrapping step
   FastDiv f_n0h, f_n1, f_n2, f_n0;
+  uint32_t site0;   // added to a site's index in its Philox counter (0 unless this
+                    // lattice is one time slab of a larger one)
 };
 
 // A site: scalar coordinates and its row; only compile-time indices are used.
@@ -507,6 +530,9 @@ __device__ __forceinline__ int hidx(const Geom& g, const Site& s) { return (s.x0
 __device__ __forceinline__ uint32_t site_index(const Geom& g, const Site& s) {
   return (uint32_t)(s.x0 + g.n[0] * s.row);
 }
+// The site word of the Philox counter: the site index, shifted by site0 for a
+// slab of a larger lattice so that its draws are the larger lattice's.
+__device__ __forceinline__ uint32_t philox_site(const Geom& g, const Site& s) { return site_index(g, s) + g.site0; }
 __device__ __forceinline__ int parity(const Site& s) { return (s.x0 + s.x1 + s.x2 + s.x3) & 1; }
 
 // Site with half-index h on the parity-p sublattice.
@@ -558,34 +584,34 @@ template <int D, int S> __device__ __forceinline__ int half_step(const Geom& g, 
 // U_nu(x-nu+mu).  U_nu(x) and U_nu(x-nu+mu) have the parity p of x; the four
 // singly shifted links have parity 1-p.  Neighbour indices come from
 // half-index steps (dmu = the step x -> x + MU).
-template <int P, int MU, int NU, bool NC, bool CP>
+template <int P, int MU, int NU, bool NC, bool CP, bool MCG = false>
 __device__ __forceinline__ void staple_term(const Links<P, CP>& L, const Geom& g, const Site& x, int h, int dmu,
                                             int p, Quat<typename Real<P>::T>& s) {
   using R = typename Real<P>::T;
   const int q = p ^ 1;
   const int h_mnu = h + half_step<NU, -1>(g, x);
-  const Quat<R> a = ldl<P, NC>(L, 2 * NU + p, h);                          // U_nu(x)
-  const Quat<R> b = ldl<P, NC>(L, 2 * MU + q, h + half_step<NU, +1>(g, x)); // U_mu(x+nu)
-  const Quat<R> c = ldl<P, NC>(L, 2 * NU + q, h + dmu);                    // U_nu(x+mu)
-  const Quat<R> d = ldl<P, NC>(L, 2 * NU + q, h_mnu);                      // U_nu(x-nu)
-  const Quat<R> e = ldl<P, NC>(L, 2 * MU + q, h_mnu);                      // U_mu(x-nu)
-  const Quat<R> f = ldl<P, NC>(L, 2 * NU + p, h_mnu + dmu);                // U_nu(x-nu+mu)
+  const Quat<R> a = ldl<P, NC>(L, 2 * NU + p, h);                                // U_nu(x)
+  const Quat<R> b = ldmu<P, NC, MCG>(L, 2 * MU + q, h + half_step<NU, +1>(g, x)); // U_mu(x+nu)
+  const Quat<R> c = ldl<P, NC>(L, 2 * NU + q, h + dmu);                          // U_nu(x+mu)
+  const Quat<R> d = ldl<P, NC>(L, 2 * NU + q, h_mnu);                            // U_nu(x-nu)
+  const Quat<R> e = ldmu<P, NC, MCG>(L, 2 * MU + q, h_mnu);                      // U_mu(x-nu)
+  const Quat<R> f = ldl<P, NC>(L, 2 * NU + p, h_mnu + dmu);                      // U_nu(x-nu+mu)
   qacc_mul_nd(s, qmul(a, b), c);
   qacc_mul(s, qmul_dn(d, e), f);
 }
 
 // Staple sum for link (x, MU) over the directions NU != MU selected by NMASK
 // (0xF: all, the heat bath), NU ascending.
-template <int P, int MU, int NMASK, bool NC, bool CP>
+template <int P, int MU, int NMASK, bool NC, bool CP, bool MCG = false>
 __device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P, CP>& L, const Geom& g,
                                                            const Site& x, int h, int p) {
   using R = typename Real<P>::T;
   Quat<R> s = qmake<R>(0, 0, 0, 0);
   const int dmu = half_step<MU, +1>(g, x);
-  if (MU != 0 && (NMASK & 1)) staple_term<P, MU, 0, NC>(L, g, x, h, dmu, p, s);
-  if (MU != 1 && (NMASK & 2)) staple_term<P, MU, 1, NC>(L, g, x, h, dmu, p, s);
-  if (MU != 2 && (NMASK & 4)) staple_term<P, MU, 2, NC>(L, g, x, h, dmu, p, s);
-  if (MU != 3 && (NMASK & 8)) staple_term<P, MU, 3, NC>(L, g, x, h, dmu, p, s);
+  if (MU != 0 && (NMASK & 1)) staple_term<P, MU, 0, NC, CP, MCG>(L, g, x, h, dmu, p, s);
+  if (MU != 1 && (NMASK & 2)) staple_term<P, MU, 1, NC, CP, MCG>(L, g, x, h, dmu, p, s);
+  if (MU != 2 && (NMASK & 4)) staple_term<P, MU, 2, NC, CP, MCG>(L, g, x, h, dmu, p, s);
+  if (MU != 3 && (NMASK & 8)) staple_term<P, MU, 3, NC, CP, MCG>(L, g, x, h, dmu, p, s);
   return s;
 }
 
@@ -593,19 +619,19 @@ __device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P, CP>& 
 // with `lower` set to the partial sum over NU < MU.  Tr(U_MU(x) lower^dagger)/2
 // is the sum of the plaquettes in the planes (NU, MU), NU < MU, that contain
 // the link (Section 2, Eq. 12).
-template <int P, int MU, bool NC, bool CP>
+template <int P, int MU, bool NC, bool CP, bool MCG = false>
 __device__ __forceinline__ Quat<typename Real<P>::T> staple_split(const Links<P, CP>& L, const Geom& g, const Site& x,
                                                                  int h, int p, Quat<typename Real<P>::T>& lower) {
   using R = typename Real<P>::T;
   Quat<R> s = qmake<R>(0, 0, 0, 0);
   const int dmu = half_step<MU, +1>(g, x);
-  if (MU != 0) staple_term<P, MU, 0, NC>(L, g, x, h, dmu, p, s);
+  if (MU != 0) staple_term<P, MU, 0, NC, CP, MCG>(L, g, x, h, dmu, p, s);
   if (MU == 1) lower = s;
-  if (MU != 1) staple_term<P, MU, 1, NC>(L, g, x, h, dmu, p, s);
+  if (MU != 1) staple_term<P, MU, 1, NC, CP, MCG>(L, g, x, h, dmu, p, s);
   if (MU == 2) lower = s;
-  if (MU != 2) staple_term<P, MU, 2, NC>(L, g, x, h, dmu, p, s);
+  if (MU != 2) staple_term<P, MU, 2, NC, CP, MCG>(L, g, x, h, dmu, p, s);
   if (MU == 3) lower = s;
-  if (MU != 3) staple_term<P, MU, 3, NC>(L, g, x, h, dmu, p, s);
+  if (MU != 3) staple_term<P, MU, 3, NC, CP, MCG>(L, g, x, h, dmu, p, s);
   if (MU == 0) lower = qmake<R>(0, 0, 0, 0);
   return s;
 }

@@ -4,6 +4,7 @@
 // Paper: Cardoso & Bicudo, arXiv:1010.4834.
 #include <type_traits>
 
+#include "su2_hb_link.cuh"
 #include "su2_internal.h"
 #include "su2_kernel_util.cuh"
 
@@ -58,42 +59,12 @@ template <int BS, bool MEAS> struct DeferCap { static constexpr int value = MEAS
 // often); fewer drains mean fewer block-wide barriers.
 template <bool MEAS> struct DeferEvery { static constexpr int value = MEAS ? 32 : 64; };
 
-template <class R> struct PlainAcc {
-  R s = R(0);
-  __device__ __forceinline__ void add(R v) { s += v; }
-  __device__ __forceinline__ double value() const { return (double)s; }
-};
-
-template <class R, bool MEAS> struct Deferred {
-  Quat<R> w;
-  R alpha;
-  int h;
-  uint32_t site;
-};
-template <class R> struct Deferred<R, true> {
-  Quat<R> w;
-  R alpha;
-  int h;
-  uint32_t site;
-  Quat<R> lower;
-};
-
-template <class R, bool MEAS>
-__device__ __forceinline__ int finish_deferred(const Deferred<R, MEAS>& d, uint4 ctr, const HBParams& hp,
-                                               Quat<R>* out) {
-  R a0;
-  const int n = sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0);
-  if (n) *out = compose_link<R>(a0, d.w, ctr, hp);
-  return n;
-}
-
 template <int P, int MU, bool MEAS, int PAR, int BS>
 __global__ void __launch_bounds__(BS, Occ<P>::hb * kThreads / BS)
     k_heatbath(Links<P, true> L, Geom g, const uint32_t* sweep_base, uint32_t sweep_off,
                const __grid_constant__ HBParams hp, unsigned long long* stats, double* meas) {
   constexpr int p = PAR;
   using R = typename Real<P>::T;
-  using M = Math<R>;
   using Def = Deferred<R, MEAS>;
   constexpr int kDeferCap = DeferCap<BS, MEAS>::value;
   constexpr int kHbThreads = BS;
@@ -102,7 +73,7 @@ __global__ void __launch_bounds__(BS, Occ<P>::hb * kThreads / BS)
   const R beta = (R)hp.beta;
   const uint32_t sweep = (sweep_base ? *sweep_base : 0u) + sweep_off;
   const uint32_t tag = (uint32_t)MU | hp.lattice_tag;
-  unsigned int trials = 0, capped = 0, haar = 0;
+  HBCount cnt;
   // MEAS: plaquettes of the planes (NU < MU, MU).  A plain sum: a thread adds
   // vh / (grid size) terms of magnitude <= 2 (about 55 on 64^4), so FP32
   // rounding stays near 1e-6 relative per thread before the FP64 block sums.
@@ -114,71 +85,10 @@ __global__ void __launch_bounds__(BS, Occ<P>::hb * kThreads / BS)
   int it = 0;
   for (int base = blockIdx.x * blockDim.x; base < vh; base += stride, ++it) {
     const int h = base + threadIdx.x;
-    if (h < vh) {
-      const Site x = site_from_half(g, (uint32_t)h, p);
-      Quat<R> lower;
-      Quat<R> sig;
-      if constexpr (MEAS) sig = staple_split<P, MU, true>(L, g, x, h, p, lower);
-      else sig = staple<P, MU, 0xF, true>(L, g, x, h, p);
-      const uint32_t site = site_index(g, x);
-      const uint4 ctr = make_uint4(site, tag, sweep, 0u);
-      const R k2 = qdot(sig, sig);
-      const R invk = M::rsqrt(k2);
-      const R alpha = beta * k2 * invk;
-      if (!(alpha >= R(1e-12))) {
-        uint4 c = ctr;
-        c.w = 1u;
-        const Quat<R> nl = haar_from<R>(philox(c, hp.rk));
-        if constexpr (MEAS) plaq.add(qdot(L.put(2 * MU + p, h, nl), lower));
-        else L.st(2 * MU + p, h, nl);
-        haar += 1;
-      } else {
-        const R inv2a = trial_inv2a(alpha);
-        const R e = trial_e(alpha, hp.sampler);
-        const Quat<R> w = qscale(sig, invk);
-        R a0;
-        if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0)) {
-          const Quat<R> nl = compose_link<R>(a0, w, ctr, hp);
-          if constexpr (MEAS) plaq.add(qdot(L.put(2 * MU + p, h, nl), lower));
-          else L.st(2 * MU + p, h, nl);
-          trials += 1;
-        } else if (hp.max_tries > 1) {
-          const int slot = atomicAdd(&qn, 1);
-          Def d;
-          d.w = w;
-          d.alpha = alpha;
-          d.h = h;
-          d.site = site;
-          if constexpr (MEAS) d.lower = lower;
-          if (slot < kDeferCap) {
-            queue[slot] = d;
-          } else {
-            Quat<R> nl;
-            const int n = finish_deferred<R, MEAS>(d, ctr, hp, &nl);
-            if constexpr (MEAS) plaq.add(qdot(n ? L.put(2 * MU + p, h, nl) : L.ld(2 * MU + p, h), lower));
-            else if (n) L.st(2 * MU + p, h, nl);
-            trials += n ? (unsigned)n : (unsigned)hp.max_tries;
-            capped += n == 0;
-          }
-        } else {
-          if constexpr (MEAS) plaq.add(qdot(L.ld(2 * MU + p, h), lower));
-          trials += 1;
-          capped += 1;
-        }
-      }
-    }
+    if (h < vh) hb_link<P, MU, MEAS, p, false, kDeferCap>(L, g, h, tag, sweep, beta, hp, queue, &qn, plaq, cnt);
     if ((it % DeferEvery<MEAS>::value) == DeferEvery<MEAS>::value - 1 || base + stride >= vh) {
       __syncthreads();
-      const int n = min(qn, kDeferCap);
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const Def d = queue[i];
-        Quat<R> nl;
-        const int t = finish_deferred<R, MEAS>(d, make_uint4(d.site, tag, sweep, 0u), hp, &nl);
-        if constexpr (MEAS) plaq.add(qdot(t ? L.put(2 * MU + p, d.h, nl) : L.ld(2 * MU + p, d.h), d.lower));
-        else if (t) L.st(2 * MU + p, d.h, nl);
-        trials += t ? (unsigned)t : (unsigned)hp.max_tries;
-        capped += t == 0;
-      }
+      hb_drain<P, MU, MEAS, p>(L, queue, min(qn, kDeferCap), tag, sweep, hp, plaq, cnt);
       __syncthreads();
       if (threadIdx.x == 0) qn = 0;
       __syncthreads();
@@ -199,9 +109,9 @@ __global__ void __launch_bounds__(BS, Occ<P>::hb * kThreads / BS)
     __shared__ unsigned int sh[3];
     if (threadIdx.x < 3) sh[threadIdx.x] = 0;
     __syncthreads();
-    if (trials) atomicAdd(&sh[0], trials);
-    if (capped) atomicAdd(&sh[1], capped);
-    if (haar) atomicAdd(&sh[2], haar);
+    if (cnt.trials) atomicAdd(&sh[0], cnt.trials);
+    if (cnt.capped) atomicAdd(&sh[1], cnt.capped);
+    if (cnt.haar) atomicAdd(&sh[2], cnt.haar);
     __syncthreads();
     if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(stats + threadIdx.x, (unsigned long long)sh[threadIdx.x]);
   }

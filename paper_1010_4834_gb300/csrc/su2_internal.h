@@ -63,8 +63,43 @@ struct SweepEpilogue {
   double* hist;
   uint32_t* sweep;
 };
+// The fused parity pair of direction mu (su2_pair.cu), FP32 and F16Q.  Its
+// control block and per-slice counts (nt of them) must be zero before the
+// first launch; every launch leaves them zero again.  `meas` as for
+// launch_heatbath (mu >= 1): the parity-1 half sums the plaquettes.
+struct PairCtl {
+  unsigned int ticket;  // next work item
+  unsigned int exits;   // blocks that have left
+  unsigned int err;     // 1: a dependency wait timed out
+  unsigned int pad[29];
+};
+struct PairShape {
+  int nt;   // time slices
+  int hs;   // half-sites (links of one class) per slice
+  int cps;  // work chunks per slice and phase
+  int lag;  // waves by which the parity-1 half trails the parity-0 half
+};
+#ifndef SU2_PAIR_LPT
+#define SU2_PAIR_LPT 1
+#endif
+#ifndef SU2_PAIR_LAG
+#define SU2_PAIR_LAG 3
+#endif
+constexpr int kPairLinksPerThread = SU2_PAIR_LPT;  // links per thread in one work chunk
+constexpr int kPairLag = SU2_PAIR_LAG;
+PairShape pair_shape(const Geom& g);
+int pair_grid(int prec);
+cudaError_t launch_heatbath_pair(const LatticeView& v, int mu, const uint32_t* sweep_base, uint32_t sweep_off,
+                                 const HBParams& hp, PairCtl* ctl, unsigned int* done0, cudaStream_t st,
+                                 double* meas = nullptr, int* meas_blocks = nullptr);
 cudaError_t launch_overrelax(const LatticeView& v, int mu, int parity, cudaStream_t st);
-cudaError_t launch_plaquette(const LatticeView& v, const Scratch& s, cudaStream_t st);
+// The plaquette means of sites [s0, s0 + ns) (ns < 0: every site) to s.out[0..2].
+cudaError_t launch_plaquette(const LatticeView& v, const Scratch& s, cudaStream_t st, int64_t s0 = 0,
+                             int64_t ns = -1);
+// Products of the time links of slices [t0, t0 + nt) of spatial sites
+// [x0, x0 + nx), FP64, 4 doubles per spatial site.
+cudaError_t launch_time_lines(const LatticeView& v, int t0, int nt, int64_t x0, int64_t nx, double* out,
+                              cudaStream_t st);
 // With `ep` the reduction partials must not overlap ep->meas.
 cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t st,
                             const SweepEpilogue* ep = nullptr);

@@ -12,7 +12,9 @@
 // the partials in a fixed order, so a result is reproducible run to run.
 #include <atomic>
 #include <cfloat>
+#include <mutex>
 
+#include "su2_hb_link.cuh"
 #include "su2_internal.h"
 #include "su2_kernel_util.cuh"
 
@@ -31,17 +33,18 @@ CaptureScope::~CaptureScope() { --g_capturing; }
 // Device info and launch shapes
 // ---------------------------------------------------------------------------
 const DeviceInfo& device_info() {
+  // filled once per device; concurrent first calls from several host
+  // threads wait on the device's once_flag
   static DeviceInfo info[64];
-  static bool have[64] = {false};
+  static std::once_flag once[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (!have[dev]) {
+  std::call_once(once[dev], [dev]() {
     cudaDeviceGetAttribute(&info[dev].sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&info[dev].l2_bytes, cudaDevAttrL2CacheSize, dev);
     if (info[dev].sms <= 0) info[dev].sms = 1;
-    have[dev] = true;
-  }
+  });
   return info[dev];
 }
 
@@ -63,6 +66,7 @@ Geom make_geom(const int n[4]) {
   g.f_n1 = FastDiv((uint32_t)n[1]);
   g.f_n2 = FastDiv((uint32_t)n[2]);
   g.f_n0 = FastDiv((uint32_t)n[0]);
+  g.site0 = 0;
   return g;
 }
 
@@ -87,30 +91,19 @@ __global__ void __launch_bounds__(kThreads) k_init(Links<P> L, Geom g, int start
     const uint32_t s = (uint32_t)(w - (int64_t)mu * V);
     const Site x = site_from_index(g, s);
     Quat<R> q = qone<R>();
-    if (start) q = haar_from<R>(philox(make_uint4(s, (uint32_t)mu | lattice_tag, 0xFFFFFFFFu, 0u), rk));
+    if (start) q = haar_from<R>(philox(make_uint4(s + g.site0, (uint32_t)mu | lattice_tag, 0xFFFFFFFFu, 0u), rk));
     L.st(2 * mu + parity(x), hidx(g, x), q);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Over-relaxation substep (Section 2, Eq. 10 with W = Sigma/|Sigma| for the
-// orientation of Eq. 11): U' = W U^dagger W keeps Tr(U Sigma^dagger).
+// Over-relaxation substep (Section 2, Eq. 10): or_link (su2_hb_link.cuh) on
+// every link of direction MU and parity PAR.
 // ---------------------------------------------------------------------------
 template <int P, int MU, int PAR>
 __global__ void __launch_bounds__(kThreads, Occ<P>::hb) k_overrelax(Links<P, true> L, Geom g) {
-  constexpr int p = PAR;
-  using R = typename Real<P>::T;
-  using M = Math<R>;
   const int stride = gridDim.x * blockDim.x;
-  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.vh; h += stride) {
-    const Site x = site_from_half(g, (uint32_t)h, p);
-    const Quat<R> sig = staple<P, MU, 0xF, true>(L, g, x, h, p);
-    const R k2 = qdot(sig, sig);
-    if (!(k2 >= M::kTiny)) continue;
-    const Quat<R> w = qscale(sig, M::rsqrt(k2));
-    const Quat<R> u = L.ld(2 * MU + p, h);
-    L.st(2 * MU + p, h, qmul(qmul_nd(w, u), w));
-  }
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.vh; h += stride) or_link<P, MU, PAR, true>(L, g, h);
 }
 
 // ---------------------------------------------------------------------------
@@ -175,14 +168,14 @@ __device__ __forceinline__ void plaq_sums(const PlaqLinks<P>& k, typename Real<P
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_plaquette(Links<P> L, Geom g, double* partials,
-                                                        unsigned int* counter, double* out) {
+__global__ void __launch_bounds__(kThreads) k_plaquette(Links<P> L, Geom g, int64_t s0, int64_t V,
+                                                        double* partials, unsigned int* counter, double* out) {
   using R = typename Real<P>::T;
   Acc<R> sp, tm;
-  const int64_t V = 2 * g.vh;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // the plaquettes of the V sites from s0 on (all sites: s0 = 0, V = volume);
   // 64-bit loop index: V may come within one stride of 2^31
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < V; s += stride) {
+  for (int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < s0 + V; s += stride) {
     PlaqLinks<P> k0;
     int p0;
     plaq_load<P>(L, g, (int)s, k0, p0);
@@ -780,11 +773,47 @@ cudaError_t launch_overrelax(const LatticeView& v, int mu, int parity, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_plaquette(const LatticeView& v, const Scratch& s, cudaStream_t st) {
+cudaError_t launch_plaquette(const LatticeView& v, const Scratch& s, cudaStream_t st, int64_t s0, int64_t ns) {
+  if (ns < 0) ns = 2 * v.g.vh;
   SU2_DISPATCH(v.prec, {
     auto L = links_of<P>(v.links, v.g.vh);
-    const int gr = grid_for(k_plaquette<P>, 2 * v.g.vh);
-    k_plaquette<P><<<gr, kThreads, 0, st>>>(L, v.g, s.partials, s.counter, s.out);
+    const int gr = grid_for(k_plaquette<P>, ns);
+    k_plaquette<P><<<gr, kThreads, 0, st>>>(L, v.g, s0, ns, s.partials, s.counter, s.out);
+  });
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Time lines (for the Polyakov loop of a lattice split into time slabs,
+// Section 2 Eqs. 14-15): for every spatial site xs in [x0, x0 + nx) the
+// product of its time links at slices t0, t0 + 1, ..., t0 + nt - 1 in that
+// order, to out[4 (xs - x0) + c] in FP64.
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_time_lines(Links<P> L, Geom g, int t0, int nt, int64_t x0, int64_t nx,
+                                                         double* out) {
+  using R = typename Real<P>::T;
+  const int64_t nsig = 2 * g.vh / g.n[3];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += stride) {
+    const int64_t xs = x0 + i;
+    Quat<R> pr = qone<R>();
+    for (int t = t0; t < t0 + nt; ++t) {
+      const Site x = site_from_index(g, (uint32_t)(xs + nsig * t));
+      pr = qmul(pr, L.ld(6 + parity(x), hidx(g, x)));
+    }
+    double* o = out + 4 * i;
+    o[0] = pr.w; o[1] = pr.x; o[2] = pr.y; o[3] = pr.z;
+  }
+}
+
+cudaError_t launch_time_lines(const LatticeView& v, int t0, int nt, int64_t x0, int64_t nx, double* out,
+                              cudaStream_t st) {
+  SU2_DISPATCH(v.prec, {
+    auto L = links_of<P>(v.links, v.g.vh);
+    const int gr = grid_for(k_time_lines<P>, nx);
+    k_time_lines<P><<<gr, kThreads, 0, st>>>(L, v.g, t0, nt, x0, nx, out);
   });
   count_launches(1);
   return cudaGetLastError();

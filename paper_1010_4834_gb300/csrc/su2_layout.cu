@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_hb_plain(float4* p, Geom g, int
     const Site x = site_from_half(g, (uint32_t)h, par);
     const Quat<float> sig = staple_at<IX, MU>(p, g, x);
     Quat<float> nl;
-    const uint4 ctr = make_uint4(site_index(g, x), tag, sweep, 0u);
+    const uint4 ctr = make_uint4(philox_site(g, x), tag, sweep, 0u);
     if (heatbath_draw<float>(sig, ctr, hp, beta, &nl) != 0) {
       const int64_t i = IX::at(g, x, MU);
       p[i] = make_float4(nl.w, nl.x, nl.y, nl.z);

