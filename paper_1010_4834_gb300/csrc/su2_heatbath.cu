@@ -52,6 +52,9 @@ namespace su2 {
 #ifndef SU2_HB_BIG_PER_SM
 #define SU2_HB_BIG_PER_SM 32768
 #endif
+#ifndef SU2_HB_LARGE_BS
+#define SU2_HB_LARGE_BS 1024
+#endif
 template <int BS, bool MEAS> struct DeferCap { static constexpr int value = MEAS ? 2 * BS : 4 * BS; };
 // Drain interval in block iterations: at the ~5% first-trial rejection of
 // beta ~ 2.5 a queue collects about 0.05 * 1024 * interval links, which the
@@ -129,7 +132,7 @@ cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint
     // the kernel is a compile-time constant: per-class base pointers
     auto L = links_of<P, true>(v.links, v.g.vh);
     const int64_t sms = device_info().sms;
-    const int bs = P != kF64 ? (v.g.vh >= (int64_t)SU2_HB_BIG_PER_SM * sms ? 1024 : 256)
+    const int bs = P != kF64 ? (v.g.vh >= (int64_t)SU2_HB_BIG_PER_SM * sms ? SU2_HB_LARGE_BS : 256)
                              : (v.g.vh >= 2 * 256 * sms ? 256 : 64);
     auto launch = [&](auto kernel, int nthreads, double* m) -> cudaError_t {
       const int gr = grid_for(kernel, v.g.vh, 0, nthreads);
@@ -144,7 +147,7 @@ cudaError_t launch_heatbath(const LatticeView& v, int mu, int parity, const uint
     auto with_bs = [&](auto meas_c, auto par_c, double* m) -> cudaError_t {
       constexpr bool M = decltype(meas_c)::value;
       constexpr int PP = decltype(par_c)::value;
-      constexpr int kSmall = P == kF64 ? 64 : 256, kLarge = P == kF64 ? 256 : 1024;
+      constexpr int kSmall = P == kF64 ? 64 : 256, kLarge = P == kF64 ? 256 : SU2_HB_LARGE_BS;
       return bs == kLarge ? launch(k_heatbath<P, MU, M, PP, kLarge>, kLarge, m)
                           : launch(k_heatbath<P, MU, M, PP, kSmall>, kSmall, m);
     };
