@@ -173,3 +173,23 @@ def test_overrelaxation_keeps_action_and_is_involution():
             np.testing.assert_allclose(B, U, atol=1e-13)
             U = A
     assert V == 256
+
+
+def test_all_cores_build_runs_the_same_chain():
+    # the OpenMP build shares the sites of each (direction, parity) class
+    # among threads; since those links do not enter each other's staples the
+    # result and the counts are those of the serial build, bit for bit
+    dims = [6, 4, 8, 4]
+    ch = oracle.chain(2.3, seed=5, max_tries=3)
+    U = oracle.init_hot(dims, ch)
+    A = U.copy()
+    sa = [oracle.sweep(dims, A, ch, sw) for sw in range(3)]
+    B = U.copy()
+    with oracle.parallel():
+        assert oracle.threads() >= 1
+        sb = [oracle.sweep(dims, B, ch, sw) for sw in range(3)]
+    assert oracle.threads() == 1
+    np.testing.assert_array_equal(A, B)
+    for x, y in zip(sa, sb):
+        assert (x.updates, x.trials, x.capped, x.haar) == (y.updates, y.trials, y.capped, y.haar)
+    assert sum(x.capped for x in sa) > 0
