@@ -201,6 +201,48 @@ def small_configs(torch):
                     "32^3x4 scan the wall time of its 16 chains run concurrently on 16 streams"}
 
 
+def oracle_per_config():
+    """The oracle as it stands on each configuration's lattice: two heat-bath
+    sweeps from its start, serial build on one core and OpenMP build on
+    every core; link updates/s (a bounded sample: the configurations' own
+    sweep counts would take minutes to hours on the CPU)."""
+    import oracle
+    from oracle import build as oracle_build
+    oracle_build.build_all()
+    cases = {"C1 8^4 beta 2.4 cold": ((8, 8, 8, 8), 2.4, "cold"), "C2 16^4 beta 2.5 hot": ((16, 16, 16, 16), 2.5, "hot"),
+             "C3 32^3x4 beta 2.4 cold": ((32, 32, 32, 4), 2.4, "cold"),
+             "C4 24^3x6 beta 2.4 hot (largest batch member)": ((24, 24, 24, 6), 2.4, "hot"),
+             "C5 64^4 beta 2.6 hot": (DIMS, BETA, "hot")}
+    out = {}
+    for name, (dims, beta, start) in cases.items():
+        row = {}
+        for label, ctx in (("1_core", None), ("all_cores", oracle.parallel)):
+            ch = oracle.chain(beta, seed=1)
+            nsw = 2 if volume(dims) <= 1 << 20 else 1
+            with (ctx() if ctx else _null()):
+                U = oracle.init_hot(list(dims), ch) if start == "hot" else oracle.init_cold(list(dims))
+                t0 = time.perf_counter()
+                if volume(dims) > 1 << 20 and label == "1_core":
+                    upd = sum(oracle.substep(list(dims), U, ch, 0, k // 2, k % 2).updates for k in range(2))
+                else:
+                    upd = sum(oracle.sweep(list(dims), U, ch, sw).updates for sw in range(nsw))
+                row[label] = upd / (time.perf_counter() - t0)
+                if label == "all_cores":
+                    row["cores"] = oracle.threads()
+        out[name] = row
+    return {"unit": UNIT, "values": out,
+            "what": "the plain FP64 C oracle, two sweeps (64^4: one sweep on all cores, two substeps on one "
+                    "core) of each configuration's lattice from its start"}
+
+
+class _null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
 def static_potential_run():
     """Section 5.4 on the 16^4 beta = 2.5 configuration: 200 configurations
     ten sweeps apart after 300 thermalisation sweeps, each smeared by 25 APE
@@ -594,6 +636,8 @@ def run_gpu_on_stream(args):
         c1 = extra["configs"]["values"]["8^4_f64_cold_100sweeps_measured"]
         extra["configs"]["8^4_f64_roofline"] = f64_roofline(c1, fp64_peak)
         extra["static_potential"] = static_potential_run()
+        if not args.no_cpu:
+            extra["oracle_configs"] = oracle_per_config()
         betas = inputs.batch_betas(len(BATCH_SHAPES), seed=1)
         b = Batch(BATCH_SHAPES, betas, seed=1, start="hot", prec="f32")
         groups = b.tune(4)

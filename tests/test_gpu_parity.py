@@ -495,6 +495,22 @@ def test_batched_tuner_keeps_the_chain():
     b.close()
 
 
+def test_batched_tuning_cache(tmp_path):
+    # the first tune times the candidates and records the winner under (GPU,
+    # precision, shapes); a batch of the same shapes (other couplings, other
+    # order) takes it from the cache without timing
+    path = str(tmp_path / "tune.json")
+    dims = [(8, 8, 8, 8), (6, 6, 6, 6), (4, 4, 4, 4), (8, 8, 8, 8)]
+    a = Batch(dims, [2.3, 2.4, 2.5, 2.2], seed=41, start="hot", prec="f32")
+    g = a.tune(2, cache=path)
+    a.close()
+    from paper_1010_4834_gb300 import tuning
+    assert list(tuning.load(path).values()) == [{"groups": g, "sweeps_timed": 2}]
+    b = Batch(dims[::-1], [2.0, 2.1, 2.6, 2.7], seed=5, start="hot", prec="f32")
+    assert b.tune(2, cache=path) == g and b.groups == g
+    b.close()
+
+
 def test_batched_matches_single_lattice_chain():
     dims = [(4, 4, 4, 4), (6, 6, 6, 4)]
     b = Batch(dims, [2.2, 2.6], seed=21, start="hot", prec="f64")

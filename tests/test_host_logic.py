@@ -120,3 +120,16 @@ def test_plateau_binning_reports_a_series_too_short():
 def test_thermalisation_drops_the_first_fifth():
     h = np.arange(100.0)[:, None] * np.ones((1, 4))
     assert ensemble.thermalised(h)[0, 0] == 20.0 and len(ensemble.thermalised(h)) == 80
+
+
+def test_tuning_cache_keys_and_round_trip(tmp_path):
+    from paper_1010_4834_gb300 import tuning
+    a = tuning.key("NVIDIA GB300", "f32", [(8, 8, 8, 8), (16, 16, 16, 16), (8, 8, 8, 8)])
+    b = tuning.key("NVIDIA GB300", "f32", [(16, 16, 16, 16), (8, 8, 8, 8), (8, 8, 8, 8)])
+    assert a == b == "NVIDIA GB300|f32|16x16x16x16*1,8x8x8x8*2"        # order-free
+    assert tuning.key("NVIDIA GB300", "f64", [(8, 8, 8, 8)]) != tuning.key("NVIDIA GB300", "f32", [(8, 8, 8, 8)])
+    p = str(tmp_path / "sub" / "tune.json")
+    assert tuning.lookup(a, p) is None
+    tuning.store(a, {"groups": 16}, p)
+    tuning.store("other", {"groups": 2}, p)
+    assert tuning.lookup(a, p) == {"groups": 16} and tuning.lookup("other", p) == {"groups": 2}
