@@ -565,6 +565,21 @@ def run_gpu_on_stream(args):
            "h2d_bytes_per_step": V * 16 * 8, "d2h_bytes_per_step": hist.nbytes + W.nbytes,
            "path": "pinned host links -> copy engine (next step's, overlapped) -> Lattice.set_links(device copy) "
                    "-> sweep_measure(100) -> ape_smear(0.7, 25) -> wilson_loops(16, 16)", "steps": e2e_steps}
+    # the same through the C ABI's own host-input path: su2_set_links reads
+    # the pinned host buffer itself (its conversion kernel reads host memory
+    # directly), so each step's copy is not overlapped with the previous step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.set_links(host_cfg.numpy())
+        lat.sweep_measure(SWEEPS, hist)
+        lat.ape_smear(APE_ALPHA, APE_STEPS)
+        W = lat.wilson_loops(RMAX, TMAX, smeared=True)
+    torch.cuda.synchronize()
+    t_dir = time.perf_counter() - t0
+    e2e["host_path"] = {"value": ws * updates_per_step * e2e_steps / t_dir, "unit": UNIT,
+                        "path": "pinned host links -> Lattice.set_links(host pointer: su2_set_links reads it "
+                                "directly) -> sweep_measure(100) -> ape_smear(0.7, 25) -> wilson_loops(16, 16)"}
     del host_cfg, dev_cfg
 
     extra = {}

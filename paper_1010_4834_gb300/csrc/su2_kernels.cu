@@ -534,6 +534,13 @@ __global__ void __launch_bounds__(kWilsonThreads) k_wilson(Links<P> Ls, Links<P>
 // for k_wilson_rt_final.
 // ---------------------------------------------------------------------------
 constexpr int kWrtT = 16;  // T values per chunk
+// The T loop unrolled by two: W(16,16) on 64^4 FP32 21.8 -> 20.4 ms (the
+// sixteen F quaternions stay in place across iterations instead of being
+// moved back at the loop edge); by four 21.7 ms.
+#ifndef SU2_WILSON_TUNROLL
+#define SU2_WILSON_TUNROLL 2
+#endif
+constexpr int kWilsonTUnroll = SU2_WILSON_TUNROLL;
 
 
 template <int P, int RC, int NTH>
@@ -618,6 +625,7 @@ __global__ void __launch_bounds__(NTH, 1) k_wilson_rt(Links<P> Ls, Links<P> Lt, 
         for (int k = 0; k < RC; ++k) F[k] = qmul(F[k], row[k]);
         tt = tt + 1 == wrap_at ? 0 : tt + 1;
       }
+#pragma unroll kWilsonTUnroll
       for (int j = 0; j < nT; ++j) {             // T = t0 + j + 1
         D = qmul(D, ut[a + W * tt]);
         {
