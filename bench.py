@@ -243,6 +243,55 @@ class _null:
         return False
 
 
+def batched_run(torch, peaks):
+    """The 64-lattice batch: tuned schedule, then 200 sweeps in one persistent
+    launch; link updates/s and the algorithmic GB/s at the substep's 128 B
+    per update against the measured copy peak, with the ncu traffic of one
+    batched launch (profiles/batched_f32.md) when it matches the source."""
+    from paper_1010_4834_gb300 import Batch, inputs
+    betas = inputs.batch_betas(len(BATCH_SHAPES), seed=1)
+    b = Batch(BATCH_SHAPES, betas, seed=1, start="hot", prec="f32")
+    groups = b.tune(4)
+    b.sweep(20)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    b.sweep(200)
+    e.record()
+    torch.cuda.synchronize()
+    tb = a.elapsed_time(e) / 1e3
+    vb = sum(volume(d) for d in BATCH_SHAPES)
+    gb = 200 * 4 * vb * 128 / tb / 1e9
+    out = {"value": 200 * 4 * vb / tb, "unit": UNIT,
+           "achieved_gbs": round(gb, 1), "frac": round(gb / peaks["hbm_gbs"], 4), "bytes_per_update": 128,
+           "what": "64 lattices (16 each of 8^4, 12^4, 16^4, 24^3x6), beta ~ U[2.0, 2.8], "
+                   "FP32, 200 sweeps in one persistent cooperative launch (CUDA graph)",
+           "ms_per_sweep": tb / 200 * 1e3, "groups": groups, "block_size": b.block_size,
+           "schedule": "lattices dealt largest-first to G groups with CTAs in proportion to their work; "
+                       "(block size, G) picked by su2_batch_tune"}
+    vals = _profile_values("batched_f32.md")
+    if vals.get("batch_sha") == batch_source_sha():
+        try:
+            out["traffic_dram_bytes_per_update"] = float(vals["dram_bytes_per_update"])
+            out["traffic_l2_bytes_per_update"] = float(vals["l2_bytes_per_update"])
+        except (KeyError, ValueError):
+            pass
+    b.close()
+    return out
+
+
+def batch_source_sha():
+    """Hash of the batched kernel's sources (code only) and build flags."""
+    h = hashlib.sha256()
+    pkg = os.path.join(ROOT, "paper_1010_4834_gb300")
+    for f in ("su2_batch.cu", "su2_device.cuh", "su2_hb_link.cuh", "su2_kernel_util.cuh", "su2_internal.h"):
+        with open(os.path.join(pkg, "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
+    with open(os.path.join(pkg, "build.py"), encoding="utf-8") as fh:
+        h.update(_code_only(fh.read(), python=True).encode())
+    return h.hexdigest()[:16]
+
+
 def static_potential_run():
     """Section 5.4 on the 16^4 beta = 2.5 configuration: 200 configurations
     ten sweeps apart after 300 thermalisation sweeps, each smeared by 25 APE
@@ -495,7 +544,7 @@ def run_gpu_on_stream(args):
     if rank == 0 or ws == 1:
         su2_build.build()
     barrier()
-    from paper_1010_4834_gb300 import Batch, Lattice, inputs, kernel_launches, probe_fma
+    from paper_1010_4834_gb300 import Lattice, kernel_launches, probe_fma
 
     V = volume(DIMS)
     lat = Lattice(DIMS, BETA, seed=1 + rank, start="hot", prec=PREC)
@@ -653,27 +702,7 @@ def run_gpu_on_stream(args):
         extra["static_potential"] = static_potential_run()
         if not args.no_cpu:
             extra["oracle_configs"] = oracle_per_config()
-        betas = inputs.batch_betas(len(BATCH_SHAPES), seed=1)
-        b = Batch(BATCH_SHAPES, betas, seed=1, start="hot", prec="f32")
-        groups = b.tune(4)
-        b.sweep(20)
-        torch.cuda.synchronize()
-        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        b.sweep(200)
-        e.record()
-        torch.cuda.synchronize()
-        tb = a.elapsed_time(e) / 1e3
-        vb = sum(volume(d) for d in BATCH_SHAPES)
-        gb = 200 * 4 * vb * 128 / tb / 1e9
-        extra["batched"] = {"value": 200 * 4 * vb / tb, "unit": UNIT,
-                            "achieved_gbs": round(gb, 1), "frac": round(gb / peaks["hbm_gbs"], 4),
-                            "bytes_per_update": 128,
-                            "what": "64 lattices (16 each of 8^4, 12^4, 16^4, 24^3x6), beta ~ U[2.0, 2.8], "
-                                    "FP32, 200 sweeps in one persistent cooperative launch (CUDA graph)",
-                            "ms_per_sweep": tb / 200 * 1e3, "groups": groups,
-                            "schedule": "lattices dealt largest-first to the groups picked by su2_batch_tune"}
-        b.close()
+        extra["batched"] = batched_run(torch, peaks)
     else:
         lat.close()
 
@@ -744,6 +773,8 @@ def main():
     ap.add_argument("--sweeps", type=int, default=None, help="sweeps per step override (profiling only)")
     ap.add_argument("--prec", choices=["f32", "f64", "f16q"], default="f32",
                     help="link precision override (profiling only; not a bench line)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the 64-lattice batched measurement and print it (profiling; not a bench line)")
     args = ap.parse_args()
     global DIMS, SWEEPS, WORKLOAD
     if args.extent:
@@ -758,6 +789,10 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.batched_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"batched": batched_run(torch, measured_peaks()[0])}), flush=True)
     else:
         run_gpu(args)
 

@@ -418,12 +418,18 @@ int su2_batch_set_overrelax(su2_batch* b, int n);
  * The schedule's group count G (1 <= G <= min(lattices, co-resident CTAs)),
  * i.e. the number of lattices swept at the same time.  The default is one
  * group per lattice (all in flight), capped at the co-resident CTAs.
- * su2_batch_tune times `sweeps` sweeps for a set of candidate G on a scratch
- * copy of the links (the chain is not advanced; it allocates and frees that
- * copy), keeps the fastest and returns it in *groups (may be NULL).
+ * su2_batch_set_block_size: threads per CTA of the batched kernel, 256 (the
+ * default) or 512 (SU2_EINVAL otherwise); the co-resident grid follows and the
+ * group count is kept, capped at the new grid.
+ * su2_batch_tune times `sweeps` sweeps for every candidate pair (block size,
+ * G) on a scratch copy of the links (the chain is not advanced; it allocates
+ * and frees that copy), keeps the fastest and returns its G in *groups (may
+ * be NULL; su2_batch_block_size gives the block size).
  */
 int su2_batch_set_groups(su2_batch* b, int groups);
 int su2_batch_groups(su2_batch* b, int* groups);
+int su2_batch_set_block_size(su2_batch* b, int threads);
+int su2_batch_block_size(su2_batch* b, int* threads);
 int su2_batch_tune(su2_batch* b, int sweeps, int* groups);
 
 /* out[3*i + k]: su2_plaquette of lattice i.  Synchronises. */

@@ -80,6 +80,8 @@ SIGNATURES = {
     "su2_batch_sweep": (_i, [_vp, _i]),
     "su2_batch_set_groups": (_i, [_vp, _i]),
     "su2_batch_groups": (_i, [_vp, _ip]),
+    "su2_batch_set_block_size": (_i, [_vp, _i]),
+    "su2_batch_block_size": (_i, [_vp, _ip]),
     "su2_batch_tune": (_i, [_vp, _i, _ip]),
     "su2_batch_plaquette": (_i, [_vp, _dp]),
     "su2_batch_polyakov": (_i, [_vp, _dp]),

@@ -98,8 +98,10 @@ __device__ __forceinline__ bool group_barrier(GroupBarrier* gb, unsigned int n, 
   return ok != 0;
 }
 
-constexpr int kBatchThreads = 256;
-constexpr int kBatchQueue = 512;
+// Block sizes the batched kernel is built for (su2_batch_set_block_size,
+// searched by su2_batch_tune); the deferral queue holds two entries a thread.
+constexpr int kBatchThreads = 256;  // default
+template <int BS> struct BatchQueue { static constexpr int value = 2 * BS; };
 
 template <class R> struct BDeferred {
   Quat<R> w;
@@ -112,7 +114,7 @@ template <class R> struct BDeferred {
 // rejected links queued and finished by the whole block at the end.  Links
 // are read with coherent loads (other CTAs of the group wrote them before the
 // last barrier).
-template <int P, int MU, int PAR>
+template <int P, int MU, int PAR, int BS>
 __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geom& g, int rank, int cpg,
                                               uint32_t sweep, uint32_t tag, typename Real<P>::T beta,
                                               const HBParams& hp, BDeferred<typename Real<P>::T>* queue, int* qn) {
@@ -120,7 +122,8 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
   using M = Math<R>;
   constexpr int p = PAR;
   const int vh = (int)g.vh;
-  for (int base = rank * kBatchThreads; base < vh; base += cpg * kBatchThreads) {
+  constexpr int kQ = BatchQueue<BS>::value;
+  for (int base = rank * BS; base < vh; base += cpg * BS) {
     const int h = base + threadIdx.x;
     if (h >= vh) continue;
     const Site x = site_from_half(g, (uint32_t)h, p);
@@ -144,7 +147,7 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
       L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, hp));
     } else if (hp.max_tries > 1) {
       const int slot = atomicAdd(qn, 1);
-      if (slot < kBatchQueue) {
+      if (slot < kQ) {
         BDeferred<R> d;
         d.w = w;
         d.alpha = alpha;
@@ -157,8 +160,8 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
     }
   }
   __syncthreads();
-  const int n = min(*qn, kBatchQueue);
-  for (int i = threadIdx.x; i < n; i += kBatchThreads) {
+  const int n = min(*qn, kQ);
+  for (int i = threadIdx.x; i < n; i += BS) {
     const BDeferred<R> d = queue[i];
     const uint4 ctr = make_uint4(d.site, tag, sweep, 0u);
     R a0;
@@ -170,22 +173,21 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
 }
 
 // One over-relaxation substep (MU, p) of one lattice by the CTAs of a group.
-template <int P, int MU, int PAR>
+template <int P, int MU, int PAR, int BS>
 __device__ __forceinline__ void batch_or_substep(const Links<P, true>& L, const Geom& g, int rank, int cpg) {
   const int vh = (int)g.vh;
-  for (int h = rank * kBatchThreads + (int)threadIdx.x; h < vh; h += cpg * kBatchThreads)
-    or_link<P, MU, PAR, false>(L, g, h);
+  for (int h = rank * BS + (int)threadIdx.x; h < vh; h += cpg * BS) or_link<P, MU, PAR, false>(L, g, h);
 }
 
-// Four blocks of 256 per SM (64 registers a thread) for FP32 / F16Q, two for FP64.
-template <int P>
-__global__ void __launch_bounds__(kBatchThreads, P == kF64 ? 2 : 4)
+// 1024 threads per SM (64 registers a thread) for FP32 / F16Q, 512 for FP64.
+template <int P, int BS>
+__global__ void __launch_bounds__(BS, (P == kF64 ? 512 : 1024) / BS)
     k_batch_groups(const BatchLattice* __restrict__ desc, const int* __restrict__ order,
                    const int4* __restrict__ plan, const int* __restrict__ cta_group, int nsweeps, int nor,
                    const uint32_t* sweep_base, const __grid_constant__ HBParams hp, GroupBarrier* bars, BatchCtl* ctl,
                    unsigned long long timeout_ns) {
   using R = typename Real<P>::T;
-  __shared__ BDeferred<R> queue[kBatchQueue];
+  __shared__ BDeferred<R> queue[BatchQueue<BS>::value];
   __shared__ int qn;
   const int group = cta_group[blockIdx.x];
   if (group < 0) return;
@@ -204,14 +206,14 @@ __global__ void __launch_bounds__(kBatchThreads, P == kF64 ? 2 : 4)
     const R beta = (R)desc[l].beta;
     const uint32_t tag = (uint32_t)mu | ((uint32_t)l << 2);
     switch (2 * mu + p) {
-      case 0: batch_substep<P, 0, 0>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 1: batch_substep<P, 0, 1>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 2: batch_substep<P, 1, 0>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 3: batch_substep<P, 1, 1>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 4: batch_substep<P, 2, 0>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 5: batch_substep<P, 2, 1>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 6: batch_substep<P, 3, 0>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      default: batch_substep<P, 3, 1>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+      case 0: batch_substep<P, 0, 0, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+      case 1: batch_substep<P, 0, 1, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+      case 2: batch_substep<P, 1, 0, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+      case 3: batch_substep<P, 1, 1, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+      case 4: batch_substep<P, 2, 0, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+      case 5: batch_substep<P, 2, 1, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+      case 6: batch_substep<P, 3, 0, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+      default: batch_substep<P, 3, 1, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
     }
   };
   // one lattice at a time, a barrier after each substep: the lattice's links
@@ -224,14 +226,14 @@ __global__ void __launch_bounds__(kBatchThreads, P == kF64 ? 2 : 4)
     Links<P, true> L;
     L.set(desc[l].links, g.vh);
     switch (2 * mu + p) {
-      case 0: batch_or_substep<P, 0, 0>(L, g, rank, cpg); break;
-      case 1: batch_or_substep<P, 0, 1>(L, g, rank, cpg); break;
-      case 2: batch_or_substep<P, 1, 0>(L, g, rank, cpg); break;
-      case 3: batch_or_substep<P, 1, 1>(L, g, rank, cpg); break;
-      case 4: batch_or_substep<P, 2, 0>(L, g, rank, cpg); break;
-      case 5: batch_or_substep<P, 2, 1>(L, g, rank, cpg); break;
-      case 6: batch_or_substep<P, 3, 0>(L, g, rank, cpg); break;
-      default: batch_or_substep<P, 3, 1>(L, g, rank, cpg); break;
+      case 0: batch_or_substep<P, 0, 0, BS>(L, g, rank, cpg); break;
+      case 1: batch_or_substep<P, 0, 1, BS>(L, g, rank, cpg); break;
+      case 2: batch_or_substep<P, 1, 0, BS>(L, g, rank, cpg); break;
+      case 3: batch_or_substep<P, 1, 1, BS>(L, g, rank, cpg); break;
+      case 4: batch_or_substep<P, 2, 0, BS>(L, g, rank, cpg); break;
+      case 5: batch_or_substep<P, 2, 1, BS>(L, g, rank, cpg); break;
+      case 6: batch_or_substep<P, 3, 0, BS>(L, g, rank, cpg); break;
+      default: batch_or_substep<P, 3, 1, BS>(L, g, rank, cpg); break;
     }
   };
   for (int li = 0; li < pl.y; ++li)
@@ -282,6 +284,7 @@ struct su2_batch {
   int graph_n;
   int grid;    // co-resident CTAs
   int groups;  // current G
+  int bs;      // threads per CTA (256 or 512)
   unsigned long long timeout_ns;
   int nor;                   // over-relaxation sweeps before each heat-bath sweep
   unsigned int fault_extra;  // injected missing barrier arrivals (0: none)
@@ -295,17 +298,20 @@ constexpr int kMaxCtas = 1 << 16;  // co-resident CTAs of the persistent grid
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-template <int P> int occupancy_blocks() {
+template <int P, int BS> int occupancy_blocks() {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_groups<P>, kBatchThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_groups<P, BS>, BS, 0);
   return per_sm;
 }
 
-int batch_grid(int prec) {
-  int per_sm = prec == kF64 ? occupancy_blocks<kF64>() : prec == kF32 ? occupancy_blocks<kF32>() : occupancy_blocks<kF16Q>();
+template <int BS> int batch_grid_bs(int prec) {
+  int per_sm = prec == kF64 ? occupancy_blocks<kF64, BS>()
+                            : prec == kF32 ? occupancy_blocks<kF32, BS>() : occupancy_blocks<kF16Q, BS>();
   if (per_sm < 1) per_sm = 1;
   return per_sm * device_info().sms;
 }
+
+int batch_grid(int prec, int bs) { return bs == 512 ? batch_grid_bs<512>(prec) : batch_grid_bs<256>(prec); }
 
 LatticeView lview(const su2_batch* b, int i) {
   LatticeView v;
@@ -420,7 +426,7 @@ cudaError_t launch_groups(const su2_batch* b, const BatchLattice* d_desc, int n,
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof cfg);
   cfg.gridDim = dim3(b->grid);
-  cfg.blockDim = dim3(kBatchThreads);
+  cfg.blockDim = dim3(b->bs);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -429,10 +435,16 @@ cudaError_t launch_groups(const su2_batch* b, const BatchLattice* d_desc, int n,
   cfg.numAttrs = 1;
   const uint32_t* sw = b->d_sweep;
   cudaError_t e;
-  switch (b->prec) {
-    case kF64: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF64>, d_desc, (const int*)b->d_order, (const int4*)b->d_plan, (const int*)b->d_cta_group, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
-    case kF32: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF32>, d_desc, (const int*)b->d_order, (const int4*)b->d_plan, (const int*)b->d_cta_group, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
-    default: e = cudaLaunchKernelEx(&cfg, k_batch_groups<kF16Q>, d_desc, (const int*)b->d_order, (const int4*)b->d_plan, (const int*)b->d_cta_group, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns); break;
+  auto go = [&](auto kernel) {
+    return cudaLaunchKernelEx(&cfg, kernel, d_desc, (const int*)b->d_order, (const int4*)b->d_plan,
+                              (const int*)b->d_cta_group, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns);
+  };
+  if (b->bs == 512) {
+    e = b->prec == kF64 ? go(k_batch_groups<kF64, 512>)
+                        : b->prec == kF32 ? go(k_batch_groups<kF32, 512>) : go(k_batch_groups<kF16Q, 512>);
+  } else {
+    e = b->prec == kF64 ? go(k_batch_groups<kF64, 256>)
+                        : b->prec == kF32 ? go(k_batch_groups<kF32, 256>) : go(k_batch_groups<kF16Q, 256>);
   }
   if (e == cudaSuccess) count_launches(1);
   return e;
@@ -564,7 +576,8 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   for (int i = 0; i < n; ++i)
     SU2_CU_CLEAN(launch_init(lview(b, i), start, key, (uint32_t)i << 2, b->stream), su2_batch_destroy(b));
   SU2_CU_CLEAN(cudaStreamSynchronize(b->stream), su2_batch_destroy(b));
-  b->grid = batch_grid(prec);
+  b->bs = kBatchThreads;
+  b->grid = batch_grid(prec, b->bs);
   int rc = set_groups(b, default_groups(b));
   if (rc) {
     su2_batch_destroy(b);
@@ -604,6 +617,29 @@ extern "C" int su2_batch_set_overrelax(su2_batch* b, int n) {
   if (n < 0 || n > 16) return fail(SU2_EINVAL, "over-relaxation sweeps per heat-bath sweep must be in 0..16");
   b->nor = n;
   drop_graph(b);
+  return SU2_OK;
+}
+
+// Threads per CTA of the batched kernel; the co-resident grid follows it and
+// the group count is kept (capped at the new grid).
+static int set_block_size(su2_batch* b, int bs) {
+  b->bs = bs;
+  b->grid = batch_grid(b->prec, bs);
+  return set_groups(b, std::min(b->groups, std::min(b->grid, b->n)));
+}
+
+extern "C" int su2_batch_set_block_size(su2_batch* b, int threads) {
+  clear_error();
+  if (!b) return fail(SU2_EINVAL, "handle is NULL");
+  if (threads != 256 && threads != 512) return fail(SU2_EINVAL, "block size must be 256 or 512");
+  DeviceGuard dg(b->device);
+  return set_block_size(b, threads);
+}
+
+extern "C" int su2_batch_block_size(su2_batch* b, int* threads) {
+  clear_error();
+  if (!b || !threads) return fail(SU2_EINVAL, "NULL argument");
+  *threads = b->bs;
   return SU2_OK;
 }
 
@@ -684,37 +720,43 @@ extern "C" int su2_batch_tune(su2_batch* b, int sweeps, int* groups) {
     cleanup();
     return fail(SU2_ECUDA, "tuning set-up failed: %s", cudaGetErrorString(e));
   }
-  const int original = b->groups;
-  std::vector<int> cand;
-  for (int G : {1, 2, 4, 8, 12, 16, 24, 32, 40, 48, 64, 96, 128}) cand.push_back(G);
-  cand.push_back(default_groups(b));
-  cand.push_back(b->n);
-  std::sort(cand.begin(), cand.end());
-  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-  int best = original;
+  const int original = b->groups, original_bs = b->bs;
+  int best = original, best_bs = original_bs;
   float best_ms = 1e30f;
-  for (int G : cand) {
-    if (G < 1 || G > b->n || G > b->grid || G > kMaxGroups) continue;
-    int rc = set_groups(b, G);
-    if (rc) { cleanup(); return rc; }
-    e = launch_groups(b, d_desc_copy, sweeps, b->stream);  // warm the schedule
-    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-    if (e == cudaSuccess) e = launch_groups(b, d_desc_copy, sweeps, b->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    if (e != cudaSuccess) {
-      cleanup();
-      set_groups(b, original);
-      return fail(SU2_ECUDA, "tuning launch failed: %s", cudaGetErrorString(e));
+  for (int bs : {256, 512}) {
+    int rc = set_block_size(b, bs);
+    if (rc) { cleanup(); set_block_size(b, original_bs); set_groups(b, original); return rc; }
+    std::vector<int> cand;
+    for (int G : {1, 2, 4, 8, 12, 16, 24, 32, 40, 48, 64, 96, 128}) cand.push_back(G);
+    cand.push_back(default_groups(b));
+    cand.push_back(b->n);
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    for (int G : cand) {
+      if (G < 1 || G > b->n || G > b->grid || G > kMaxGroups) continue;
+      rc = set_groups(b, G);
+      if (rc) { cleanup(); return rc; }
+      e = launch_groups(b, d_desc_copy, sweeps, b->stream);  // warm the schedule
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+      if (e == cudaSuccess) e = launch_groups(b, d_desc_copy, sweeps, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        cleanup();
+        set_block_size(b, original_bs);
+        set_groups(b, original);
+        return fail(SU2_ECUDA, "tuning launch failed: %s", cudaGetErrorString(e));
+      }
+      int rc2 = check_ctl(b, b->sweep);
+      if (rc2) { cleanup(); set_block_size(b, original_bs); set_groups(b, original); return rc2; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best = G; best_bs = bs; }
     }
-    int rc2 = check_ctl(b, b->sweep);
-    if (rc2) { cleanup(); set_groups(b, original); return rc2; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) { best_ms = ms; best = G; }
   }
   cleanup();
-  int rc = set_groups(b, best);
+  int rc = set_block_size(b, best_bs);
+  if (!rc) rc = set_groups(b, best);
   if (rc) return rc;
   if (groups) *groups = best;
   return SU2_OK;

@@ -62,8 +62,20 @@ template <int BS, bool MEAS> struct DeferCap { static constexpr int value = MEAS
 // often); fewer drains mean fewer block-wide barriers.
 template <bool MEAS> struct DeferEvery { static constexpr int value = MEAS ? 32 : 64; };
 
+// Minimum resident blocks per SM (the register budget): 1024 threads per SM
+// at 64 registers, except for the large-block FP32 / F16Q configuration when
+// SU2_HB_LARGE_MINB overrides it.
+#ifndef SU2_HB_LARGE_MINB
+#define SU2_HB_LARGE_MINB 0
+#endif
+template <int P, int BS> struct HbMinBlocks {
+  static constexpr int value = (P != kF64 && BS == SU2_HB_LARGE_BS && SU2_HB_LARGE_MINB > 0)
+                                   ? SU2_HB_LARGE_MINB
+                                   : (Occ<P>::hb * kThreads / BS > 0 ? Occ<P>::hb * kThreads / BS : 1);
+};
+
 template <int P, int MU, bool MEAS, int PAR, int BS>
-__global__ void __launch_bounds__(BS, Occ<P>::hb * kThreads / BS)
+__global__ void __launch_bounds__(BS, HbMinBlocks<P, BS>::value)
     k_heatbath(Links<P, true> L, Geom g, const uint32_t* sweep_base, uint32_t sweep_off,
                const __grid_constant__ HBParams hp, unsigned long long* stats, double* meas) {
   constexpr int p = PAR;

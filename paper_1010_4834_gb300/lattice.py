@@ -301,8 +301,19 @@ class Batch:
     def groups(self, g):
         check(_lib.load().su2_batch_set_groups(self._h, int(g)))
 
+    @property
+    def block_size(self):
+        t = C.c_int()
+        check(_lib.load().su2_batch_block_size(self._h, C.byref(t)))
+        return t.value
+
+    @block_size.setter
+    def block_size(self, threads):
+        check(_lib.load().su2_batch_set_block_size(self._h, int(threads)))
+
     def tune(self, sweeps=4, cache=False):
-        """Pick the fastest group count on a scratch copy; returns it.  With
+        """Pick the fastest (block size, group count) on a scratch copy;
+        returns the group count (block_size gives the other).  With
         cache (True, or a file path) a group count recorded for this GPU,
         precision and set of shapes is applied without timing, and a new
         result is recorded (paper_1010_4834_gb300.tuning)."""
@@ -314,12 +325,13 @@ class Batch:
             k = tuning.key(torch.cuda.get_device_name(), self.prec_name, self.dims)
             hit = tuning.lookup(k, path)
             if hit is not None:
+                self.block_size = int(hit.get("block_size", 256))
                 self.groups = int(hit["groups"])
                 return self.groups
         g = C.c_int()
         check(_lib.load().su2_batch_tune(self._h, int(sweeps), C.byref(g)))
         if k is not None:
-            tuning.store(k, {"groups": g.value, "sweeps_timed": int(sweeps)}, path)
+            tuning.store(k, {"groups": g.value, "block_size": self.block_size, "sweeps_timed": int(sweeps)}, path)
         return g.value
 
     def plaquette(self):

@@ -1,7 +1,7 @@
 """Cache of tuned batched-sweep schedules.
 
-su2_batch_tune times candidate group counts on a scratch copy of a batch's
-links and keeps the fastest.  The choice depends only on the GPU, the link
+su2_batch_tune times candidate (block size, group count) pairs on a scratch
+copy of a batch's links and keeps the fastest.  The choice depends only on the GPU, the link
 precision and the multiset of lattice shapes (couplings change acceptance
 rates, not the work per sweep), so it is stored under that key in a JSON
 file and reused by later batches of the same composition instead of being

@@ -465,10 +465,11 @@ def test_batched_result_is_independent_of_the_schedule():
     dims = [(4, 4, 4, 4), (6, 4, 4, 2), (8, 8, 8, 8), (6, 6, 6, 4), (4, 4, 2, 8)]
     betas = [2.0, 2.5, 2.7, 0.0, 2.2]
     ref = None
-    for G in (1, 2, 3, 5):
+    for G, bs in ((1, 256), (2, 512), (3, 256), (5, 512)):
         b = Batch(dims, betas, seed=31, start="hot", prec="f32")
+        b.block_size = bs
         b.groups = G
-        assert b.groups == G
+        assert b.groups == G and b.block_size == bs
         b.sweep(3)
         links = [b.get_links(i) for i in range(len(dims))]
         b.close()
@@ -503,11 +504,13 @@ def test_batched_tuning_cache(tmp_path):
     dims = [(8, 8, 8, 8), (6, 6, 6, 6), (4, 4, 4, 4), (8, 8, 8, 8)]
     a = Batch(dims, [2.3, 2.4, 2.5, 2.2], seed=41, start="hot", prec="f32")
     g = a.tune(2, cache=path)
-    a.close()
     from paper_1010_4834_gb300 import tuning
-    assert list(tuning.load(path).values()) == [{"groups": g, "sweeps_timed": 2}]
+    bs = a.block_size
+    a.close()
+    assert bs in (256, 512)
+    assert list(tuning.load(path).values()) == [{"groups": g, "block_size": bs, "sweeps_timed": 2}]
     b = Batch(dims[::-1], [2.0, 2.1, 2.6, 2.7], seed=5, start="hot", prec="f32")
-    assert b.tune(2, cache=path) == g and b.groups == g
+    assert b.tune(2, cache=path) == g and b.groups == g and b.block_size == bs
     b.close()
 
 
