@@ -70,10 +70,11 @@ double oracle_u01(uint32_t x, int u23) {
   return ldexp((double)x + 0.5, -32);
 }
 
-/* Four uniforms of draw `draw` for link (s, mu) in sweep `sweep`. */
-void oracle_draw(const oracle_chain* c, long s, int mu, uint32_t sweep, uint32_t draw,
-                 double u[4]) {
-  uint32_t ctr[4], key[2], r[4];
+/* The four Philox words of draw `draw` for link (s, mu) in sweep `sweep`:
+ * counter (s, mu | lattice_id << 2, sweep, draw), key = the 64-bit seed. */
+void oracle_draw_words(const oracle_chain* c, long s, int mu, uint32_t sweep, uint32_t draw,
+                       uint32_t r[4]) {
+  uint32_t ctr[4], key[2];
   ctr[0] = (uint32_t)s;
   ctr[1] = (uint32_t)mu | (c->lattice_id << 2);
   ctr[2] = sweep;
@@ -81,6 +82,13 @@ void oracle_draw(const oracle_chain* c, long s, int mu, uint32_t sweep, uint32_t
   key[0] = (uint32_t)(c->seed & 0xffffffffu);
   key[1] = (uint32_t)(c->seed >> 32);
   oracle_philox4x32_10(ctr, key, r);
+}
+
+/* Four uniforms of draw `draw` for link (s, mu) in sweep `sweep`. */
+void oracle_draw(const oracle_chain* c, long s, int mu, uint32_t sweep, uint32_t draw,
+                 double u[4]) {
+  uint32_t r[4];
+  oracle_draw_words(c, s, mu, sweep, draw, r);
   for (int i = 0; i < 4; i++) u[i] = oracle_u01(r[i], c->u23);
 }
 
@@ -300,7 +308,15 @@ int oracle_sample_a0(const oracle_chain* c, double alpha, long s, int mu, uint32
  * the vector part uniform on the sphere of radius sqrt(1 - a0^2).  The new
  * link is U = X W (Eq. 9 with the sampled matrix in place of U).
  *
- * Direction: Philox draw 0, cos(theta) = 2 u0 - 1, phi = 2 pi u1.
+ * Direction (uniform on the 2-sphere; the paper fixes no random numbers):
+ *   - 32-bit mode: Philox draw 0, cos(theta) = 2 u0 - 1, phi = 2 pi u1;
+ *   - 23-bit mode (the FP32 map): the nine low bits of each word of the
+ *     accepting trial's draw n, which its 23-bit uniforms do not use:
+ *     c = (r0 mod 2^9) 2^9 + (r1 mod 2^9), f = (r2 mod 2^9) 2^9 + (r3 mod 2^9),
+ *     cos(theta) = (2c + 1) 2^-18 - 1, phi = 2 pi (f + 1/2) 2^-18.  These bits
+ *     are independent of the trial's uniforms, so the direction is still
+ *     independent of a0; cos(theta) and phi are uniform on grids of 2^18
+ *     midpoints.
  * Readings where the paper is silent:
  *   - all trials failing keeps the old link.  The accepted-value kernel is
  *     proportional to the target and independent of the old link, so the
@@ -330,11 +346,21 @@ int oracle_heatbath_link(const oracle_chain* c, long s, int mu, uint32_t sweep,
     for (int i = 0; i < 4; i++) new_link[i] = old_link[i];
     return 0;
   }
-  double u[4];
-  oracle_draw(c, s, mu, sweep, 0u, u);
-  double cos_theta = 2.0 * u[0] - 1.0;
+  double cos_theta, phi;
+  if (c->u23) {
+    uint32_t r[4];
+    oracle_draw_words(c, s, mu, sweep, (uint32_t)n, r);
+    uint32_t cb = ((r[0] & 0x1FFu) << 9) | (r[1] & 0x1FFu);
+    uint32_t fb = ((r[2] & 0x1FFu) << 9) | (r[3] & 0x1FFu);
+    cos_theta = ldexp(2.0 * cb + 1.0, -18) - 1.0;
+    phi = two_pi * ldexp(fb + 0.5, -18);
+  } else {
+    double u[4];
+    oracle_draw(c, s, mu, sweep, 0u, u);
+    cos_theta = 2.0 * u[0] - 1.0;
+    phi = two_pi * u[1];
+  }
   double sin_theta = sqrt(fmax(0.0, 1.0 - cos_theta * cos_theta));
-  double phi = two_pi * u[1];
   double r = sqrt(fmax(0.0, 1.0 - a0 * a0));
   double x[4], w[4];
   x[0] = a0;

@@ -17,7 +17,9 @@
  *           (Section 2, Eq. 1).
  *   Philox  key = (seed & 0xffffffff, seed >> 32);
  *           ctr = (s, mu | lattice_id << 2, sweep, draw).
- *           Hot start uses sweep = 0xFFFFFFFF, draw 0.
+ *           Hot start uses sweep = 0xFFFFFFFF, draw 0.  Heat-bath trial n
+ *           uses draw n; the direction draw 0 (32-bit map) or the accepting
+ *           trial's low bits (23-bit map, the FP32 comparison).
  *
  * Every function below names the passage of the paper it follows.  Where the
  * paper is silent the reading taken is stated at the function.
@@ -40,7 +42,9 @@ typedef struct {
   uint32_t lattice_id;  /* batch member, 0 for a single lattice              */
   int max_tries;        /* cap on sampler trials, >= 1                       */
   int sampler;          /* ORACLE_KP or ORACLE_CREUTZ                        */
-  int u23;              /* 0: uniforms with 32-bit resolution, 1: 23-bit     */
+  int u23;              /* 0: uniforms with 32-bit resolution, direction    */
+                        /* from draw 0; 1 (the FP32 map): 23-bit uniforms,  */
+                        /* direction from the accepting trial's low bits    */
 } oracle_chain;
 
 /* Counts collected by a substep or sweep. */
@@ -57,6 +61,8 @@ int oracle_threads(void);
 /* --- random numbers ---------------------------------------------------- */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double oracle_u01(uint32_t x, int u23);
+void oracle_draw_words(const oracle_chain* c, long s, int mu, uint32_t sweep, uint32_t draw,
+                       uint32_t r[4]);
 void oracle_draw(const oracle_chain* c, long s, int mu, uint32_t sweep, uint32_t draw,
                  double u[4]);
 

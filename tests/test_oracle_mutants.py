@@ -60,6 +60,12 @@ MUTANTS = [
      lambda tmp: chn.test_2d_exact_plaquette(2.0)),
     ("hot start phase", "z[1] = r01 * sin(two_pi * u[1]);", "z[1] = r01 * sin(two_pi * u[0]);",
      lambda tmp: chn.test_hot_start_from_raw_philox()),
+    ("fp32 direction from the trial's own bits", "uint32_t cb = ((r[0] & 0x1FFu) << 9) | (r[1] & 0x1FFu);",
+     "uint32_t cb = r[0] >> 14;",
+     lambda tmp: smp.test_single_link_heatbath_distribution_fp32_map()),
+    ("fp32 direction cosine scale", "cos_theta = ldexp(2.0 * cb + 1.0, -18) - 1.0;",
+     "cos_theta = ldexp(cb + 0.5, -18) - 1.0;",
+     lambda tmp: smp.test_single_link_heatbath_distribution_fp32_map()),
     ("draw keying", "ctr[1] = (uint32_t)mu | (c->lattice_id << 2);", "ctr[1] = (uint32_t)mu | (c->lattice_id << 3);",
      lambda tmp: rng.test_draw_keying()),
 ]

@@ -5,7 +5,10 @@ Targets fixed by the mathematics, not by the oracle:
     integrated numerically here;
   * <a0> = I2(alpha)/I1(alpha) (the normaliser is pi I1(alpha)/alpha and its
     alpha-derivative gives the first moment);
-  * the vector part of X = U_new W^dagger uniform on the 2-sphere (Eq. 7).
+  * the vector part of X = U_new W^dagger uniform on the 2-sphere (Eq. 7) and
+    independent of a0 (the density exp(beta k x0) dX factorises), in both
+    uniform maps; in the 23-bit map cos(theta) lies on the grid of 2^18
+    midpoints of [-1, 1].
 """
 import numpy as np
 import pytest
@@ -61,17 +64,17 @@ def _unit(q):
     return q / np.linalg.norm(q)
 
 
-def test_single_link_heatbath_distribution():
+def _link_samples(u23, nsamp=30000):
     rng = np.random.default_rng(9)
     sigma = 2.3 * _unit(rng.standard_normal(4)) + 0.4 * _unit(rng.standard_normal(4))
     k = np.linalg.norm(sigma)
     beta = 2.1
-    ch = oracle.chain(beta, seed=17)
+    ch = oracle.chain(beta, seed=17, u23=u23)
     old = _unit(rng.standard_normal(4))
     a0s, vecs = [], []
     w = sigma / k
     wd = oracle.qdag(w)
-    for sweep in range(30000):
+    for sweep in range(nsamp):
         n, new, _ = oracle.heatbath_link(ch, 3, 1, sweep, sigma, old)
         assert n > 0
         assert abs(new @ new - 1.0) < 1e-14
@@ -79,13 +82,30 @@ def test_single_link_heatbath_distribution():
         a0s.append(new @ sigma / k)         # (1/2) Tr(U_new Sigma^dagger) / k
         assert abs(x[0] - a0s[-1]) < 1e-13
         vecs.append(x[1:] / np.linalg.norm(x[1:]))
-    a0s, vecs = np.array(a0s), np.array(vecs)
-    assert stats.kstest(a0s, target_cdf(beta * k)).pvalue > 1e-3
-    # uniform direction on S^2: mean 0, second moments delta_ij / 3
+    return ch, sigma, old, beta * k, np.array(a0s), np.array(vecs)
+
+
+def test_single_link_heatbath_distribution(u23=0):
+    ch, sigma, old, alpha, a0s, vecs = _link_samples(u23)
+    k = np.linalg.norm(sigma)
+    wd = oracle.qdag(sigma / k)
+    assert stats.kstest(a0s, target_cdf(alpha)).pvalue > 1e-3
+    # uniform direction on S^2: mean 0, second moments delta_ij / 3, and
+    # each component (= cos of the angle to that axis) uniform on [-1, 1]
     n = len(vecs)
     assert np.all(np.abs(vecs.mean(0)) < 5 / np.sqrt(3 * n))
     M = vecs.T @ vecs / n
     assert np.all(np.abs(M - np.eye(3) / 3) < 5 * np.sqrt(2 / 15 / n) + 1e-3)
+    for i in range(3):
+        assert stats.kstest(vecs[:, i], stats.uniform(-1, 2).cdf).pvalue > 1e-3
+    # independence of a0 and the direction: a 4 x 4 contingency table of a0
+    # quartiles against cos(theta) quartiles, and against phi quartiles
+    qa = np.searchsorted(np.quantile(a0s, [0.25, 0.5, 0.75]), a0s)
+    for comp in (vecs[:, 2], np.arctan2(vecs[:, 1], vecs[:, 0])):
+        qc = np.searchsorted(np.quantile(comp, [0.25, 0.5, 0.75]), comp)
+        table = np.zeros((4, 4))
+        np.add.at(table, (qa, qc), 1)
+        assert stats.chi2_contingency(table).pvalue > 1e-3
     # power check: composing with the wrong staple orientation
     # (U = X W^dagger) gives a statistic the same test rejects
     wrong = []
@@ -93,7 +113,38 @@ def test_single_link_heatbath_distribution():
         _, new, _ = oracle.heatbath_link(ch, 3, 1, sweep, sigma, old)
         x = oracle.qmul(new, wd)
         wrong.append(oracle.qmul(x, wd) @ sigma / k)
-    assert stats.kstest(np.array(wrong), target_cdf(beta * k)).pvalue < 1e-6
+    assert stats.kstest(np.array(wrong), target_cdf(alpha)).pvalue < 1e-6
+
+
+def test_single_link_heatbath_distribution_fp32_map():
+    test_single_link_heatbath_distribution(u23=1)
+
+
+def test_fp32_map_direction_grid():
+    # 23-bit map: cos(theta) = (2c + 1) 2^-18 - 1 for an integer c < 2^18 (the
+    # z component of the unit vector part of X), a grid no 32-bit direction
+    # lands on; the 32-bit map's values are off it
+    for u23, on_grid in ((1, True), (0, False)):
+        *_, vecs = _link_samples(u23, nsamp=400)
+        c = ((vecs[:, 2] + 1.0) * 2.0 ** 18 - 1.0) / 2.0
+        off = np.abs(c - np.round(c))
+        assert np.all(np.round(c) >= 0) and np.all(np.round(c) < 2 ** 18)
+        if on_grid:
+            assert off.max() < 1e-4, off.max()
+        else:
+            assert np.median(off) > 0.1
+
+
+def test_direction_power_check():
+    # the contingency test separates a direction that depends on a0: the
+    # cos(theta) of X tilted towards a0 fails it
+    _, _, _, _, a0s, vecs = _link_samples(1, nsamp=8000)
+    z = np.clip(vecs[:, 2] + 0.3 * (a0s - a0s.mean()) / a0s.std(), -1, 1)
+    qa = np.searchsorted(np.quantile(a0s, [0.25, 0.5, 0.75]), a0s)
+    qc = np.searchsorted(np.quantile(z, [0.25, 0.5, 0.75]), z)
+    table = np.zeros((4, 4))
+    np.add.at(table, (qa, qc), 1)
+    assert stats.chi2_contingency(table).pvalue < 1e-6
 
 
 def test_haar_branch_and_cap():
