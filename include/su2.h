@@ -23,7 +23,10 @@
  *            (site, mu | lattice_id << 2, sweep, draw).  The hot start uses
  *            sweep index 0xFFFFFFFF.  Heat-bath sweep i (counted from 0 since
  *            the start) uses sweep index i, so a resumed chain replays the
- *            same stream.
+ *            same stream.  Trial n of a link uses draw n; its direction on
+ *            the sphere comes from draw 0 (F64) or from the nine low bits of
+ *            each word of the accepting trial's draw (F32, F16Q: the bits
+ *            their 23-bit uniforms leave unused).
  *   device   links live on the device in a structure of arrays: for each
  *            direction mu and parity p, a contiguous array of the V/2 links
  *            of that class, ordered by s >> 1.  Element: 2 x double2 (F64),

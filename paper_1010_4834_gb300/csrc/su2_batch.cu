@@ -143,8 +143,9 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
     const R e = trial_e(alpha, hp.sampler);
     const Quat<R> w = qscale(sig, invk);
     R a0;
-    if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0)) {
-      L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, hp));
+    uint4 rt;
+    if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0, &rt)) {
+      L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, rt, hp));
     } else if (hp.max_tries > 1) {
       const int slot = atomicAdd(qn, 1);
       if (slot < kQ) {
@@ -154,8 +155,8 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
         d.h = h;
         d.site = site;
         queue[slot] = d;
-      } else if (sample_a0_from<R>(2, alpha, inv2a, e, ctr, hp, &a0)) {
-        L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, hp));
+      } else if (sample_a0_from<R>(2, alpha, inv2a, e, ctr, hp, &a0, &rt)) {
+        L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, rt, hp));
       }
     }
   }
@@ -165,8 +166,9 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
     const BDeferred<R> d = queue[i];
     const uint4 ctr = make_uint4(d.site, tag, sweep, 0u);
     R a0;
-    if (sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0))
-      L.st(2 * MU + p, d.h, compose_link<R>(a0, d.w, ctr, hp));
+    uint4 rt;
+    if (sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0, &rt))
+      L.st(2 * MU + p, d.h, compose_link<R>(a0, d.w, ctr, rt, hp));
   }
   __syncthreads();
   if (threadIdx.x == 0) *qn = 0;

@@ -48,8 +48,10 @@ template <class R, bool MEAS>
 __device__ __forceinline__ int finish_deferred(const Deferred<R, MEAS>& d, uint4 ctr, const HBParams& hp,
                                                Quat<R>* out) {
   R a0;
-  const int n = sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0);
-  if (n) *out = compose_link<R>(a0, d.w, ctr, hp);
+  uint4 rt;
+  const int n =
+      sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0, &rt);
+  if (n) *out = compose_link<R>(a0, d.w, ctr, rt, hp);
   return n;
 }
 
@@ -89,8 +91,9 @@ __device__ __forceinline__ void hb_link(const Links<P, CP>& L, const Geom& g, in
   const R e = trial_e(alpha, hp.sampler);
   const Quat<R> w = qscale(sig, invk);
   R a0;
-  if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0)) {
-    const Quat<R> nl = compose_link<R>(a0, w, ctr, hp);
+  uint4 rt;
+  if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0, &rt)) {
+    const Quat<R> nl = compose_link<R>(a0, w, ctr, rt, hp);
     if constexpr (MEAS) plaq.add(qdot(L.put(2 * MU + p, h, nl), lower));
     else L.st(2 * MU + p, h, nl);
     cnt.trials += 1;
