@@ -329,10 +329,13 @@ def timed_sweeps(torch, lat, n, reps=3):
 def launch_seconds(torch, lat, kind, sweeps=4):
     """Average duration of one heat-bath launch of `kind` ("substep" or
     "pair"): one CUDA-event pair around the launches of `sweeps` sweeps
-    issued back to back on the lattice's stream (the way a sweep runs them),
-    and, for comparison, the mean of the same launches each bracketed by its
-    own events with the stream idle between them (which adds the launch
-    latency to every launch)."""
+    issued back to back on the lattice's stream, and, for comparison, the
+    mean of the same launches each bracketed by its own events with the
+    stream idle between them (which adds the launch latency to every launch).
+    For the substep a third figure: one event pair around 32 plain sweeps
+    replayed as the library's sweep graph (8 substep launches a sweep, plus
+    one sweep-counter bump every 8 sweeps), the way the benchmark's sweeps
+    run the kernel; that one is returned first."""
     def one(mu, p, sw):
         if kind == "pair":
             lat.pair(mu, sw)
@@ -350,6 +353,16 @@ def launch_seconds(torch, lat, kind, sweeps=4):
     torch.cuda.synchronize()
     n = 4 * len(parities) * sweeps
     back_to_back = a.elapsed_time(b) / 1e3 / n
+    in_graph = None
+    if kind != "pair":
+        lat.sweep(8)                      # the sweep graph exists
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lat.sweep(32)
+        b.record()
+        torch.cuda.synchronize()
+        in_graph = a.elapsed_time(b) / 1e3 / (8 * 32)
     times = []
     for sw in range(sweeps):
         for mu in range(4):
@@ -360,7 +373,7 @@ def launch_seconds(torch, lat, kind, sweeps=4):
                 b.record()
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(b) / 1e3)
-    return back_to_back, n, statistics.mean(times)
+    return back_to_back, n, statistics.mean(times), in_graph
 
 
 def heatbath_roofline(torch, lat, kind, peaks, peak_kind):
@@ -370,7 +383,10 @@ def heatbath_roofline(torch, lat, kind, peaks, peak_kind):
     parity pair reads 3.5 V and writes V for V updates (4.5 transfers)."""
     V = volume(DIMS)
     lb = {"f32": 16, "f64": 32, "f16q": 8}[PREC]
-    t_launch, n_launch, t_isolated = launch_seconds(torch, lat, kind)
+    t_direct, n_launch, t_isolated, t_graph = launch_seconds(torch, lat, kind)
+    t_launch = t_graph if t_graph is not None else t_direct
+    timing = ("one event pair around 32 sweeps replayed as the sweep graph (256 launches)" if t_graph is not None
+              else "one event pair around %d back-to-back launches" % n_launch)
     if kind == "pair":
         upd_launch, per_update, name = V, 4.5 * lb, "k_heatbath_pair<F32>"
     else:
@@ -382,7 +398,9 @@ def heatbath_roofline(torch, lat, kind, peaks, peak_kind):
             "peak_kind": peak_kind, "traffic": profiled_traffic(kind, upd_launch),
             "algorithmic_bytes_per_update": per_update,
             "algorithmic_bytes_per_launch": alg_bytes, "launch_us": round(t_launch * 1e6, 2),
-            "launches_timed": n_launch, "timing": "one event pair around %d back-to-back launches" % n_launch,
+            "launches_timed": 256 if t_graph is not None else n_launch, "timing": timing,
+            "launch_us_direct": round(t_direct * 1e6, 2),
+            "launch_us_direct_note": "one event pair around %d back-to-back direct launches" % n_launch,
             "launch_us_isolated": round(t_isolated * 1e6, 2),
             "updates_per_s_in_kernel": upd_launch / t_launch}
 

@@ -385,9 +385,11 @@ int su2_load(su2_lattice** h, const char* path, int prec, void* cuda_stream);
  * ------------------------------------------------------------------------- */
 
 /*
- * dims: n x 4 extents (each lattice obeys the su2_init rules), betas: n
- * couplings >= 0, 1 <= n <= 1023.  Cold or hot start per lattice.  prec: SU2_F32
- * or SU2_F64 or SU2_F16Q.
+ * dims: n x 4 extents (each lattice obeys the su2_init rules and has fewer
+ * than 2^30 sites, since the batched kernel addresses a lattice's links by
+ * 32-bit offsets; SU2_EINVAL otherwise), betas: n couplings >= 0,
+ * 1 <= n <= 1023.  Cold or hot start per lattice.  prec: SU2_F32 or SU2_F64
+ * or SU2_F16Q.
  */
 int su2_batch_init(su2_batch** b, int n, const int* dims, const double* betas, uint64_t seed,
                    int start, int prec, void* cuda_stream);

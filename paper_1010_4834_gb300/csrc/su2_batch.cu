@@ -115,7 +115,7 @@ template <class R> struct BDeferred {
 // are read with coherent loads (other CTAs of the group wrote them before the
 // last barrier).
 template <int P, int MU, int PAR, int BS>
-__device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geom& g, int rank, int cpg,
+__device__ __forceinline__ void batch_substep(const Links<P, kClassOff>& L, const Geom& g, int rank, int cpg,
                                               uint32_t sweep, uint32_t tag, typename Real<P>::T beta,
                                               const HBParams& hp, BDeferred<typename Real<P>::T>* queue, int* qn) {
   using R = typename Real<P>::T;
@@ -176,7 +176,7 @@ __device__ __forceinline__ void batch_substep(const Links<P, true>& L, const Geo
 
 // One over-relaxation substep (MU, p) of one lattice by the CTAs of a group.
 template <int P, int MU, int PAR, int BS>
-__device__ __forceinline__ void batch_or_substep(const Links<P, true>& L, const Geom& g, int rank, int cpg) {
+__device__ __forceinline__ void batch_or_substep(const Links<P, kClassOff>& L, const Geom& g, int rank, int cpg) {
   const int vh = (int)g.vh;
   for (int h = rank * BS + (int)threadIdx.x; h < vh; h += cpg * BS) or_link<P, MU, PAR, false>(L, g, h);
 }
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(BS, (P == kF64 ? 512 : 1024) / BS)
   // one substep (mu, p) of lattice l by this group's CTAs
   auto substep = [&](int l, uint32_t sweep, int mu, int p) {
     const Geom g = desc[l].g;
-    Links<P, true> L;
+    Links<P, kClassOff> L;
     L.set(desc[l].links, g.vh);
     const R beta = (R)desc[l].beta;
     const uint32_t tag = (uint32_t)mu | ((uint32_t)l << 2);
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(BS, (P == kF64 ? 512 : 1024) / BS)
   // `nor` over-relaxation sweeps precede each heat-bath sweep
   auto or_substep = [&](int l, int mu, int p) {
     const Geom g = desc[l].g;
-    Links<P, true> L;
+    Links<P, kClassOff> L;
     L.set(desc[l].links, g.vh);
     switch (2 * mu + p) {
       case 0: batch_or_substep<P, 0, 0, BS>(L, g, rank, cpg); break;
@@ -496,6 +496,9 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
     int rc = check_dims(dims + 4 * i);
     if (rc) return rc;
     if (!(betas[i] >= 0.0) || betas[i] != betas[i] || betas[i] > 1e300) return fail(SU2_EINVAL, "beta[%d] must be finite and >= 0", i);
+    // the batched kernel addresses a lattice's links by 32-bit offsets (kClassOff)
+    const int64_t v = (int64_t)dims[4 * i] * dims[4 * i + 1] * dims[4 * i + 2] * dims[4 * i + 3];
+    if (4 * v >= ((int64_t)1 << 32)) return fail(SU2_EINVAL, "lattice %d: a batch member must have fewer than 2^30 sites", i);
   }
   su2_batch* b = new (std::nothrow) su2_batch();
   if (!b) return fail(SU2_ENOMEM, "host allocation failed");

@@ -349,21 +349,30 @@ __device__ __forceinline__ int heatbath_draw(const Quat<R>& sigma, uint4 ctr, co
 // kernel writes the element); ldc() is a plain coherent load for kernels that
 // write links other blocks read after a grid barrier.
 // ---------------------------------------------------------------------------
-// CP selects the addressing: with CP a class starts at its own base pointer
-// c[cls] (kernel parameters), so a load is one multiply-add of the 32-bit
-// element index onto a constant; this is for kernels in which every class
-// index is a compile-time constant (a runtime index into c[] would force the
-// array into local memory).  Without CP a class starts at p + cls * vh.
-template <int P, bool CP = false> struct Links;
+// CP selects the addressing:
+//   kFlat      class cls starts at p + cls * vh;
+//   kClassPtr  a class starts at its own base pointer c[cls] (kernel
+//              parameters), so a load is one multiply-add of the 32-bit
+//              element index onto a constant;
+//   kClassOff  link i of class cls is element o[cls] + i of one base p, with
+//              32-bit offsets o[cls] = cls * vh (only while 8 vh < 2^32): one
+//              64-bit base in registers for all classes; 64-lattice batch
+//              40.6 -> 41.9 G updates/s against kClassPtr.
+// The last two are for kernels in which every class index is a compile-time
+// constant (a runtime index into c[] or o[] would put the array into local
+// memory).
+enum AddrMode { kFlat = 0, kClassPtr = 1, kClassOff = 2 };
+template <int P, int CP = kFlat> struct Links;
 
-template <bool CP> struct Links<kF64, CP> {
+template <int CP> struct Links<kF64, CP> {
   using E = double2;
   double2* p;     // 2 double2 per link
   int64_t vh;     // links per class
   double2* c[8];  // start of each class (filled by set())
+  uint32_t o[8];  // link offset of each class from p (kClassOff)
   // start of class cls, and link i of the class that starts at b
   __device__ __forceinline__ double2* cls_base(int cls) const {
-    if constexpr (CP) return c[cls];
+    if constexpr (CP == kClassPtr) return c[cls];
     else return p + 2 * cls * vh;
   }
   static __device__ __forceinline__ Quat<double> ldp(const double2* b, uint32_t i) {
@@ -373,10 +382,14 @@ template <bool CP> struct Links<kF64, CP> {
   __host__ __device__ void set(void* base, int64_t n) {
     p = static_cast<double2*>(base);
     vh = n;
-    for (int k = 0; k < 8; ++k) c[k] = p + 2 * k * n;
+    for (int k = 0; k < 8; ++k) {
+      c[k] = p + 2 * k * n;
+      o[k] = (uint32_t)(k * n);
+    }
   }
   __device__ __forceinline__ double2* at(int cls, int i) const {
-    if constexpr (CP) return c[cls] + 2 * (uint32_t)i;
+    if constexpr (CP == kClassOff) return p + 2 * (uint64_t)(uint32_t)(o[cls] + (uint32_t)i);
+    else if constexpr (CP == kClassPtr) return c[cls] + 2 * (uint32_t)i;
     else return p + 2 * (cls * vh + (uint32_t)i);
   }
   __device__ __forceinline__ Quat<double> ld(int cls, int i) const {
@@ -406,13 +419,14 @@ template <bool CP> struct Links<kF64, CP> {
   }
 };
 
-template <bool CP> struct Links<kF32, CP> {
+template <int CP> struct Links<kF32, CP> {
   using E = float4;
   float4* p;
   int64_t vh;
   float4* c[8];
+  uint32_t o[8];
   __device__ __forceinline__ float4* cls_base(int cls) const {
-    if constexpr (CP) return c[cls];
+    if constexpr (CP == kClassPtr) return c[cls];
     else return p + cls * vh;
   }
   static __device__ __forceinline__ Quat<float> ldp(const float4* b, uint32_t i) {
@@ -422,10 +436,14 @@ template <bool CP> struct Links<kF32, CP> {
   __host__ __device__ void set(void* base, int64_t n) {
     p = static_cast<float4*>(base);
     vh = n;
-    for (int k = 0; k < 8; ++k) c[k] = p + k * n;
+    for (int k = 0; k < 8; ++k) {
+      c[k] = p + k * n;
+      o[k] = (uint32_t)(k * n);
+    }
   }
   __device__ __forceinline__ float4* at(int cls, int i) const {
-    if constexpr (CP) return c[cls] + (uint32_t)i;
+    if constexpr (CP == kClassOff) return p + (uint32_t)(o[cls] + (uint32_t)i);
+    else if constexpr (CP == kClassPtr) return c[cls] + (uint32_t)i;
     else return p + cls * vh + (uint32_t)i;
   }
   __device__ __forceinline__ Quat<float> ld(int cls, int i) const {
@@ -450,23 +468,28 @@ template <bool CP> struct Links<kF32, CP> {
 };
 
 // binary16 quaternion, re-normalised in FP32 on every load.
-template <bool CP> struct Links<kF16Q, CP> {
+template <int CP> struct Links<kF16Q, CP> {
   using E = uint2;
   uint2* p;
   int64_t vh;
   uint2* c[8];
+  uint32_t o[8];
   __device__ __forceinline__ uint2* cls_base(int cls) const {
-    if constexpr (CP) return c[cls];
+    if constexpr (CP == kClassPtr) return c[cls];
     else return p + cls * vh;
   }
   static __device__ __forceinline__ Quat<float> ldp(const uint2* b, uint32_t i) { return unpack(__ldg(b + i)); }
   __host__ __device__ void set(void* base, int64_t n) {
     p = static_cast<uint2*>(base);
     vh = n;
-    for (int k = 0; k < 8; ++k) c[k] = p + k * n;
+    for (int k = 0; k < 8; ++k) {
+      c[k] = p + k * n;
+      o[k] = (uint32_t)(k * n);
+    }
   }
   __device__ __forceinline__ uint2* at(int cls, int i) const {
-    if constexpr (CP) return c[cls] + (uint32_t)i;
+    if constexpr (CP == kClassOff) return p + (uint32_t)(o[cls] + (uint32_t)i);
+    else if constexpr (CP == kClassPtr) return c[cls] + (uint32_t)i;
     else return p + cls * vh + (uint32_t)i;
   }
   __device__ __forceinline__ Quat<float> ld(int cls, int i) const { return unpack(__ldg(at(cls, i))); }
@@ -495,7 +518,7 @@ template <bool CP> struct Links<kF16Q, CP> {
   }
 };
 
-template <int P, bool NC, bool CP>
+template <int P, bool NC, int CP>
 __device__ __forceinline__ Quat<typename Real<P>::T> ldl(const Links<P, CP>& L, int cls, int i) {
   return NC ? L.ld(cls, i) : L.ldc(cls, i);
 }
@@ -505,7 +528,7 @@ __device__ __forceinline__ Quat<typename Real<P>::T> ldl(const Links<P, CP>& L, 
 // that class earlier in the same launch (the fused parity pair), another
 // SM's write is visible in L2 after its release, while an L1 line read
 // before it could be stale.
-template <int P, bool NC, bool MCG, bool CP>
+template <int P, bool NC, bool MCG, int CP>
 __device__ __forceinline__ Quat<typename Real<P>::T> ldmu(const Links<P, CP>& L, int cls, int i) {
   if constexpr (MCG) return L.ldcg(cls, i);
   else return ldl<P, NC>(L, cls, i);
@@ -626,7 +649,7 @@ template <int D, int S> __device__ __forceinline__ int half_step(const Geom& g, 
 // U_nu(x-nu+mu).  U_nu(x) and U_nu(x-nu+mu) have the parity p of x; the four
 // singly shifted links have parity 1-p.  Neighbour indices come from
 // half-index steps (dmu = the step x -> x + MU).
-template <int P, int MU, int NU, bool NC, bool CP, bool MCG = false>
+template <int P, int MU, int NU, bool NC, int CP, bool MCG = false>
 __device__ __forceinline__ void staple_term(const Links<P, CP>& L, const Geom& g, const Site& x, int h, int dmu,
                                             int p, Quat<typename Real<P>::T>& s) {
   using R = typename Real<P>::T;
@@ -644,7 +667,7 @@ __device__ __forceinline__ void staple_term(const Links<P, CP>& L, const Geom& g
 
 // Staple sum for link (x, MU) over the directions NU != MU selected by NMASK
 // (0xF: all, the heat bath), NU ascending.
-template <int P, int MU, int NMASK, bool NC, bool CP, bool MCG = false>
+template <int P, int MU, int NMASK, bool NC, int CP, bool MCG = false>
 __device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P, CP>& L, const Geom& g,
                                                            const Site& x, int h, int p) {
   using R = typename Real<P>::T;
@@ -661,7 +684,7 @@ __device__ __forceinline__ Quat<typename Real<P>::T> staple(const Links<P, CP>& 
 // with `lower` set to the partial sum over NU < MU.  Tr(U_MU(x) lower^dagger)/2
 // is the sum of the plaquettes in the planes (NU, MU), NU < MU, that contain
 // the link (Section 2, Eq. 12).
-template <int P, int MU, bool NC, bool CP, bool MCG = false>
+template <int P, int MU, bool NC, int CP, bool MCG = false>
 __device__ __forceinline__ Quat<typename Real<P>::T> staple_split(const Links<P, CP>& L, const Geom& g, const Site& x,
                                                                  int h, int p, Quat<typename Real<P>::T>& lower) {
   using R = typename Real<P>::T;

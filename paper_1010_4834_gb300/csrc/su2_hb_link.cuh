@@ -25,13 +25,16 @@ template <class R> struct PlainAcc {
   __device__ __forceinline__ double value() const { return (double)s; }
 };
 
-template <class R, bool MEAS> struct Deferred {
+// Queue entries are 16-byte aligned (FP32: 28 -> 32 bytes), so an entry
+// moves in a few wide shared-memory accesses: 64^4 FP32 sweep 1412 -> 1407
+// us, F16Q 1610 -> 1592 us.
+template <class R, bool MEAS> struct __align__(16) Deferred {
   Quat<R> w;
   R alpha;
   int h;
   uint32_t site;
 };
-template <class R> struct Deferred<R, true> {
+template <class R> struct __align__(16) Deferred<R, true> {
   Quat<R> w;
   R alpha;
   int h;
@@ -59,7 +62,7 @@ __device__ __forceinline__ int finish_deferred(const Deferred<R, MEAS>& d, uint4
 // atomicAdd(qn, 1) when it is below CAP.  MCG: the staple's loads of the
 // other-parity MU class bypass L1 (the fused pair kernel writes that class
 // earlier in the same launch).
-template <int P, int MU, bool MEAS, int PAR, bool MCG, int CAP, bool CP>
+template <int P, int MU, bool MEAS, int PAR, bool MCG, int CAP, int CP>
 __device__ __forceinline__ void hb_link(const Links<P, CP>& L, const Geom& g, int h, uint32_t tag, uint32_t sweep,
                                         typename Real<P>::T beta, const HBParams& hp,
                                         Deferred<typename Real<P>::T, MEAS>* queue, int* qn,
@@ -123,7 +126,7 @@ __device__ __forceinline__ void hb_link(const Links<P, CP>& L, const Geom& g, in
 }
 
 // Finish the queue entries i = threadIdx.x, threadIdx.x + blockDim.x, ... < n.
-template <int P, int MU, bool MEAS, int PAR, bool CP>
+template <int P, int MU, bool MEAS, int PAR, int CP>
 __device__ __forceinline__ void hb_drain(const Links<P, CP>& L, const Deferred<typename Real<P>::T, MEAS>* queue, int n,
                                          uint32_t tag, uint32_t sweep, const HBParams& hp,
                                          PlainAcc<typename Real<P>::T>& plaq, HBCount& cnt) {
@@ -149,7 +152,7 @@ __device__ __forceinline__ void hb_drain(const Links<P, CP>& L, const Deferred<t
 // on load) therefore normalises U' before storing it; in FP64 the walk stays
 // near 1e-15 and the update is stored as computed, like the oracle's.  NC:
 // read-only loads (no other block of the launch writes these links).
-template <int P, int MU, int PAR, bool NC, bool CP>
+template <int P, int MU, int PAR, bool NC, int CP>
 __device__ __forceinline__ void or_link(const Links<P, CP>& L, const Geom& g, int h) {
   constexpr int p = PAR;
   using R = typename Real<P>::T;

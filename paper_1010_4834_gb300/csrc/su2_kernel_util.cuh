@@ -144,7 +144,7 @@ __device__ __forceinline__ void plaquette_from_block_sums(const double* meas, in
 template <int P> struct Occ { static constexpr int hb = SU2_HB_MINB; };
 template <> struct Occ<kF64> { static constexpr int hb = 2; };
 
-template <int P, bool CP = false> static Links<P, CP> links_of(void* base, int64_t vh) {
+template <int P, int CP = kFlat> static Links<P, CP> links_of(void* base, int64_t vh) {
   Links<P, CP> L;
   L.set(base, vh);
   return L;

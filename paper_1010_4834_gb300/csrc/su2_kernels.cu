@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_init(Links<P> L, Geom g, int start
 // every link of direction MU and parity PAR.
 // ---------------------------------------------------------------------------
 template <int P, int MU, int PAR>
-__global__ void __launch_bounds__(kThreads, Occ<P>::hb) k_overrelax(Links<P, true> L, Geom g) {
+__global__ void __launch_bounds__(kThreads, Occ<P>::hb) k_overrelax(Links<P, kClassPtr> L, Geom g) {
   const int stride = gridDim.x * blockDim.x;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.vh; h += stride) or_link<P, MU, PAR, true>(L, g, h);
 }
@@ -221,10 +221,10 @@ template <> struct PolyMinBlocks<kF64> { static constexpr int value = 2; };
 
 template <int P>
 __global__ void __launch_bounds__(kThreads, PolyMinBlocks<P>::value)
-    k_polyakov(Links<P, true> L, Geom g, int lg, double* partials, unsigned int* counter, double* out,
+    k_polyakov(Links<P, kClassPtr> L, Geom g, int lg, double* partials, unsigned int* counter, double* out,
                SweepEpilogue ep) {
   using R = typename Real<P>::T;
-  using LT = Links<P, true>;
+  using LT = Links<P, kClassPtr>;
   constexpr int C = 8;
   __shared__ Quat<R> seg_prod[kThreads];
   Acc<R> acc;
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, PolyMinBlocks<P>::value)
 // backward.  blockIdx.y = parity.
 // ---------------------------------------------------------------------------
 template <int P, int MU, int NU>
-__device__ __forceinline__ void ape_pair(const Links<P, true>& L, int h, int p, const int (&dp)[3], const int (&dm)[3],
+__device__ __forceinline__ void ape_pair(const Links<P, kClassPtr>& L, int h, int p, const int (&dp)[3], const int (&dm)[3],
                                          const Quat<typename Real<P>::T>& umu, const Quat<typename Real<P>::T>& unu,
                                          Quat<typename Real<P>::T>& smu, Quat<typename Real<P>::T>& snu) {
   using R = typename Real<P>::T;
@@ -316,7 +316,7 @@ __device__ __forceinline__ void ape_pair(const Links<P, true>& L, int h, int p, 
 }
 
 template <int P>
-__device__ __forceinline__ void ape_store(const Links<P, true>& dst, int cls, int h, const Quat<typename Real<P>::T>& u,
+__device__ __forceinline__ void ape_store(const Links<P, kClassPtr>& dst, int cls, int h, const Quat<typename Real<P>::T>& u,
                                           const Quat<typename Real<P>::T>& sig, typename Real<P>::T c0,
                                           typename Real<P>::T c1) {
   using R = typename Real<P>::T;
@@ -332,7 +332,7 @@ __device__ __forceinline__ void ape_store(const Links<P, true>& dst, int cls, in
 // The sites of parity PAR (a template parameter, so every class index is a
 // compile-time constant for the per-class base pointers).
 template <int P, int PAR>
-__device__ __forceinline__ void ape_sites(const Links<P, true>& src, const Links<P, true>& dst, const Geom& g,
+__device__ __forceinline__ void ape_sites(const Links<P, kClassPtr>& src, const Links<P, kClassPtr>& dst, const Geom& g,
                                           typename Real<P>::T c0, typename Real<P>::T c1) {
   using R = typename Real<P>::T;
   constexpr int p = PAR;
@@ -357,7 +357,7 @@ __device__ __forceinline__ void ape_sites(const Links<P, true>& src, const Links
 
 template <int P>
 __global__ void __launch_bounds__(kThreads, P == kF64 ? 2 : SU2_APE3_MINB)
-    k_ape(Links<P, true> src, Links<P, true> dst, Geom g, double alpha_d) {
+    k_ape(Links<P, kClassPtr> src, Links<P, kClassPtr> dst, Geom g, double alpha_d) {
   using R = typename Real<P>::T;
   const R alpha = (R)alpha_d;
   const R c0 = R(1) - alpha, c1 = R(0.25) * alpha;
@@ -768,7 +768,7 @@ cudaError_t launch_init(const LatticeView& v, int start, PhiloxKey key, uint32_t
 
 cudaError_t launch_overrelax(const LatticeView& v, int mu, int parity, cudaStream_t st) {
   SU2_DISPATCH(v.prec, SU2_DISPATCH_MU(mu, {
-    auto L = links_of<P, true>(v.links, v.g.vh);
+    auto L = links_of<P, kClassPtr>(v.links, v.g.vh);
     if (parity == 0) {
       const int gr = grid_for(k_overrelax<P, MU, 0>, v.g.vh);
       k_overrelax<P, MU, 0><<<gr, kThreads, 0, st>>>(L, v.g);
@@ -831,7 +831,7 @@ cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t
   SweepEpilogue e{};
   if (ep) e = *ep;
   SU2_DISPATCH(v.prec, {
-    auto L = links_of<P, true>(v.links, v.g.vh);
+    auto L = links_of<P, kClassPtr>(v.links, v.g.vh);
     const int64_t nsig = 2 * v.g.vh / v.g.n[3];
     // segments per time line: the largest power of two <= 8 that divides nt
     // and leaves segments of at least 8 links
@@ -846,8 +846,8 @@ cudaError_t launch_polyakov(const LatticeView& v, const Scratch& s, cudaStream_t
 
 cudaError_t launch_ape(const LatticeView& src, void* dst, double alpha, cudaStream_t st) {
   SU2_DISPATCH(src.prec, {
-    auto S = links_of<P, true>(src.links, src.g.vh);
-    auto D = links_of<P, true>(dst, src.g.vh);
+    auto S = links_of<P, kClassPtr>(src.links, src.g.vh);
+    auto D = links_of<P, kClassPtr>(dst, src.g.vh);
     // two y-slices (one per parity) share the machine
     int gx = grid_for(k_ape<P>, 2 * src.g.vh) / 2;
     if (gx < 1) gx = 1;

@@ -153,7 +153,7 @@ __device__ __forceinline__ bool wait_for_item(unsigned int t, unsigned int total
 
 template <int P, int MU, bool MEAS>
 __global__ void __launch_bounds__(kPairThreads, kPairBlocksPerSM)
-    k_heatbath_pair(Links<P, true> L, Geom g, const uint32_t* sweep_base, uint32_t sweep_off,
+    k_heatbath_pair(Links<P, kClassPtr> L, Geom g, const uint32_t* sweep_base, uint32_t sweep_off,
                     const __grid_constant__ HBParams hp, PairCtl* ctl, unsigned int* done0, PairShape shp,
                     unsigned long long timeout_ns, double* meas) {
   using R = typename Real<P>::T;
@@ -283,7 +283,7 @@ static void pair_launch(const LatticeView& v, int grid, const uint32_t* sweep_ba
                         const HBParams& hp, PairCtl* ctl, unsigned int* done0, const PairShape& shp, cudaStream_t st,
                         double* meas) {
   const unsigned long long timeout_ns = 1000000000ull;
-  const auto L = links_of<P, true>(v.links, v.g.vh);
+  const auto L = links_of<P, kClassPtr>(v.links, v.g.vh);
   if constexpr (MU >= 1) {
     if (meas) {
       k_heatbath_pair<P, MU, true><<<grid, kPairThreads, 0, st>>>(L, v.g, sweep_base, sweep_off, hp, ctl, done0, shp,

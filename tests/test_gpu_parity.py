@@ -461,6 +461,13 @@ def test_batched_sweep_parity(prec):
     b.close()
 
 
+def test_batched_rejects_a_member_beyond_32_bit_offsets():
+    # 512^3 x 8 = 2^30 sites (a valid single lattice): the batched kernel's
+    # 32-bit link offsets do not reach it; rejected before anything is allocated
+    with pytest.raises(SU2Error, match="2\\^30"):
+        Batch([(8, 8, 8, 8), (512, 512, 512, 8)], [2.3, 2.3], seed=1, prec="f32")
+
+
 def test_batched_result_is_independent_of_the_schedule():
     dims = [(4, 4, 4, 4), (6, 4, 4, 2), (8, 8, 8, 8), (6, 6, 6, 4), (4, 4, 2, 8)]
     betas = [2.0, 2.5, 2.7, 0.0, 2.2]
