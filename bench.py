@@ -143,7 +143,7 @@ def small_configs(torch):
     run once as specified (their own sweep counts and measurements) and
     reported as link updates/s over the device time of the whole run."""
     import numpy as np
-    from paper_1010_4834_gb300 import Lattice
+    from paper_1010_4834_gb300 import Batch, Lattice
 
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -196,9 +196,24 @@ def small_configs(torch):
         out["32^3x4_%s_16betas_1000sweeps_measured" % prec] = 16 * 1000 * 4 * 32 ** 3 * 4 / t
         for x in lats:
             x.close()
+        # the same scan as one batch: one persistent launch sweeps and
+        # measures all 16 chains (su2_batch_sweep_measure); a first batch
+        # picks the schedule, a fresh one from the hot start is timed
+        betas = [float(b) for b in np.linspace(2.2, 2.6, 16)]
+        warm = Batch([(32, 32, 32, 4)] * 16, betas, seed=1, start="hot", prec=prec)
+        warm.tune(4)
+        bs, G = warm.block_size, warm.groups
+        warm.sweep_measure(16)
+        warm.close()
+        bat = Batch([(32, 32, 32, 4)] * 16, betas, seed=1, start="hot", prec=prec)
+        bat.block_size, bat.groups = bs, G
+        t = timed(lambda: bat.sweep_measure(1000))
+        out["32^3x4_%s_16betas_1000sweeps_measured_batched" % prec] = 16 * 1000 * 4 * 32 ** 3 * 4 / t
+        bat.close()
     return {"unit": UNIT, "values": out,
             "what": "each configuration's whole run (sweeps and its measurements): device time, and for the "
-                    "32^3x4 scan the wall time of its 16 chains run concurrently on 16 streams"}
+                    "32^3x4 scan the wall time of its 16 chains run concurrently on 16 streams, or (_batched) the "
+                    "device time of one batch of the 16 chains measured in one persistent launch"}
 
 
 def oracle_per_config():

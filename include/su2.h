@@ -437,6 +437,22 @@ int su2_batch_set_block_size(su2_batch* b, int threads);
 int su2_batch_block_size(su2_batch* b, int* threads);
 int su2_batch_tune(su2_batch* b, int sweeps, int* groups);
 
+/*
+ * n measured sweeps (n >= 1): the chain of su2_batch_sweep(b, n), and after
+ * each sweep s of this call and each lattice i the lattice's plaquette
+ * (all, spatial, space-time; Section 2, Eq. 12) and Polyakov loop
+ * (Eqs. 14-15) as su2_sweep_measure gives them, in
+ * hist[(s * n_lattices + i) * 4 + k] (host, n * n_lattices * 4 doubles,
+ * owned by the caller).  One persistent cooperative launch: after the eight
+ * substeps of a lattice's sweep its group adds the plaquettes at, and the
+ * time-ordered products of time links through, its share of the sites, and
+ * the group's first CTA adds the CTAs' sums in a fixed order (the values
+ * depend on the group count only through that order).  Allocates and frees
+ * a device buffer of the history's size; synchronises.  SU2_ETIMEOUT as for
+ * su2_batch_sweep (hist is then not written).
+ */
+int su2_batch_sweep_measure(su2_batch* b, int n, double* hist);
+
 /* out[3*i + k]: su2_plaquette of lattice i.  Synchronises. */
 int su2_batch_plaquette(su2_batch* b, double* out);
 /* out[i]: su2_polyakov of lattice i.  Synchronises. */

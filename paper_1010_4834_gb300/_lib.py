@@ -78,6 +78,7 @@ SIGNATURES = {
     "su2_batch_set_options": (_i, [_vp, _i, _i]),
     "su2_batch_set_overrelax": (_i, [_vp, _i]),
     "su2_batch_sweep": (_i, [_vp, _i]),
+    "su2_batch_sweep_measure": (_i, [_vp, _i, _dp]),
     "su2_batch_set_groups": (_i, [_vp, _i]),
     "su2_batch_groups": (_i, [_vp, _ip]),
     "su2_batch_set_block_size": (_i, [_vp, _i]),

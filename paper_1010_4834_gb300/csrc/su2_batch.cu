@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "su2.h"
@@ -103,73 +104,30 @@ __device__ __forceinline__ bool group_barrier(GroupBarrier* gb, unsigned int n, 
 constexpr int kBatchThreads = 256;  // default
 template <int BS> struct BatchQueue { static constexpr int value = 2 * BS; };
 
-template <class R> struct BDeferred {
-  Quat<R> w;
-  R alpha;
-  int h;
-  uint32_t site;
-};
-
-// One substep (MU, p) of one lattice by the CTAs of a group: trial 1 inline,
-// rejected links queued and finished by the whole block at the end.  Links
-// are read with coherent loads (other CTAs of the group wrote them before the
-// last barrier).
-template <int P, int MU, int PAR, int BS>
+// One substep (MU, p) of one lattice by the CTAs of a group, each link by
+// hb_link with coherent loads (other CTAs of the group wrote the links
+// before the last barrier): trial 1 inline, rejected links queued and
+// finished by the whole block at the end.  MEAS (odd substeps of MU >= 1 in
+// a measured sweep): plaq accumulates Tr(U_MU(x) L(x)^dagger)/2 with L the
+// staple's partial sum over NU < MU, as in the single-lattice substep.
+template <int P, int MU, int PAR, int BS, bool MEAS>
 __device__ __forceinline__ void batch_substep(const Links<P, kClassOff>& L, const Geom& g, int rank, int cpg,
                                               uint32_t sweep, uint32_t tag, typename Real<P>::T beta,
-                                              const HBParams& hp, BDeferred<typename Real<P>::T>* queue, int* qn) {
+                                              const HBParams& hp, void* queue_mem, int* qn,
+                                              PlainAcc<typename Real<P>::T>& plaq) {
   using R = typename Real<P>::T;
-  using M = Math<R>;
-  constexpr int p = PAR;
-  const int vh = (int)g.vh;
+  using Def = Deferred<R, MEAS>;
+  Def* queue = static_cast<Def*>(queue_mem);
   constexpr int kQ = BatchQueue<BS>::value;
+  HBCount cnt;
+  const int vh = (int)g.vh;
   for (int base = rank * BS; base < vh; base += cpg * BS) {
     const int h = base + threadIdx.x;
-    if (h >= vh) continue;
-    const Site x = site_from_half(g, (uint32_t)h, p);
-    const Quat<R> sig = staple<P, MU, 0xF, false>(L, g, x, h, p);
-    const uint32_t site = philox_site(g, x);
-    const uint4 ctr = make_uint4(site, tag, sweep, 0u);
-    const R k2 = qdot(sig, sig);
-    const R invk = M::rsqrt(k2);
-    const R alpha = beta * k2 * invk;
-    if (!(alpha >= R(1e-12))) {
-      uint4 c = ctr;
-      c.w = 1u;
-      L.st(2 * MU + p, h, haar_from<R>(philox(c, hp.rk)));
-      continue;
-    }
-    const R inv2a = trial_inv2a(alpha);
-    const R e = trial_e(alpha, hp.sampler);
-    const Quat<R> w = qscale(sig, invk);
-    R a0;
-    uint4 rt;
-    if (trial_a0<R>(alpha, inv2a, e, ctr, 1, hp, &a0, &rt)) {
-      L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, rt, hp));
-    } else if (hp.max_tries > 1) {
-      const int slot = atomicAdd(qn, 1);
-      if (slot < kQ) {
-        BDeferred<R> d;
-        d.w = w;
-        d.alpha = alpha;
-        d.h = h;
-        d.site = site;
-        queue[slot] = d;
-      } else if (sample_a0_from<R>(2, alpha, inv2a, e, ctr, hp, &a0, &rt)) {
-        L.st(2 * MU + p, h, compose_link<R>(a0, w, ctr, rt, hp));
-      }
-    }
+    if (h < vh)
+      hb_link<P, MU, MEAS, PAR, false, kQ, kClassOff, false>(L, g, h, tag, sweep, beta, hp, queue, qn, plaq, cnt);
   }
   __syncthreads();
-  const int n = min(*qn, kQ);
-  for (int i = threadIdx.x; i < n; i += BS) {
-    const BDeferred<R> d = queue[i];
-    const uint4 ctr = make_uint4(d.site, tag, sweep, 0u);
-    R a0;
-    uint4 rt;
-    if (sample_a0_from<R>(2, d.alpha, trial_inv2a(d.alpha), trial_e(d.alpha, hp.sampler), ctr, hp, &a0, &rt))
-      L.st(2 * MU + p, d.h, compose_link<R>(a0, d.w, ctr, rt, hp));
-  }
+  hb_drain<P, MU, MEAS, PAR, kClassOff, false>(L, queue, min(*qn, kQ), tag, sweep, hp, plaq, cnt);
   __syncthreads();
   if (threadIdx.x == 0) *qn = 0;
 }
@@ -181,16 +139,108 @@ __device__ __forceinline__ void batch_or_substep(const Links<P, kClassOff>& L, c
   for (int h = rank * BS + (int)threadIdx.x; h < vh; h += cpg * BS) or_link<P, MU, PAR, false>(L, g, h);
 }
 
-// 1024 threads per SM (64 registers a thread) for FP32 / F16Q, 512 for FP64.
+// Measured sweeps.  The plaquette (Eq. 12) comes from the sweep's odd
+// substeps of MU = 1, 2 (spatial planes) and MU = 3 (space-time planes), each
+// thread's sums ps and pt; at the end of the last of them every CTA writes
+// its block sums to part[4 blockIdx.x + 0, 1].  The Polyakov loop (Eqs.
+// 14-15) of the sweep's final links is taken during the first substep of
+// the lattice's next sweep, which changes no time link (over-relaxation or
+// heat bath of MU = 0): each CTA multiplies the time links of its spatial
+// sites in increasing t and writes its sum of (1/2) Tr to
+// part[4 blockIdx.x + 2].  After that substep's barrier the group's first
+// CTA adds the CTAs' sums (warp 0, a fixed lane assignment and tree) into
+// the history; a lattice's last sweep of the call takes its Polyakov loop
+// after one more barrier.  Coherent loads throughout: other CTAs of the
+// group write links during the launch.
+template <int BS>
+__device__ __forceinline__ void block_sums_to(double v0, double v1, double* out0, double* out1) {
+  __shared__ double sh[BS / 32][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  if (lane == 0) {
+    sh[warp][0] = v0;
+    sh[warp][1] = v1;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const double t0 = warp_sum(lane < BS / 32 ? sh[lane][0] : 0.0);
+    const double t1 = warp_sum(lane < BS / 32 ? sh[lane][1] : 0.0);
+    if (lane == 0) {
+      *out0 = t0;
+      if (out1) *out1 = t1;
+    }
+  }
+  __syncthreads();
+}
+
 template <int P, int BS>
-__global__ void __launch_bounds__(BS, (P == kF64 ? 512 : 1024) / BS)
+__device__ __forceinline__ void batch_polyakov_part(const Links<P, kClassOff>& L, const Geom& g, int rank, int cpg,
+                                                    double* part) {
+  using R = typename Real<P>::T;
+  Acc<R> pl;
+  const int nsig = g.n[0] * g.n[1] * g.n[2];
+  const int nt = g.n[3];
+  for (int xs = rank * BS + (int)threadIdx.x; xs < nsig; xs += cpg * BS) {
+    const int p0 = parity(site_from_index(g, (uint32_t)xs));   // parity of (xs, t = 0)
+    const uint32_t h0 = (uint32_t)xs >> 1, hstep = (uint32_t)nsig >> 1;
+    Quat<R> pr = qone<R>();
+    // nt is even: the loads of two slices are issued before their products
+    for (int t = 0; t < nt; t += 2) {
+      const Quat<R> a = L.ldc(6 + p0, h0 + hstep * t);
+      const Quat<R> b = L.ldc(6 + (p0 ^ 1), h0 + hstep * (t + 1));
+      pr = qmul(qmul(pr, a), b);
+    }
+    pl.add(pr.w);
+  }
+  block_sums_to<BS>(pl.value(), 0.0, part + 4 * (size_t)blockIdx.x + 2, nullptr);
+}
+
+// The history entry of one sweep from the group's CTA sums (warp 0 of the
+// group's first CTA).
+__device__ __forceinline__ void batch_history(const double* part, int cta0, int cpg, const Geom& g, double* o) {
+  const int lane = threadIdx.x & 31;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int r = lane; r < cpg; r += 32) {
+    const double* q = part + 4 * (size_t)(cta0 + r);
+    a += __ldcg(q);
+    b += __ldcg(q + 1);
+    c += __ldcg(q + 2);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  if (lane == 0) {
+    const double n3 = 3.0 * (double)(2 * g.vh);
+    o[0] = (a + b) / (2.0 * n3);
+    o[1] = a / n3;
+    o[2] = b / n3;
+    o[3] = c / (double)(g.n[0] * g.n[1] * g.n[2]);
+  }
+}
+
+// 1024 threads per SM (64 registers a thread) for FP32 / F16Q, 512 for FP64.
+// MEAS: measured sweeps (su2_batch_sweep_measure), a separate instantiation
+// so that the plain sweep's kernel carries none of the measurement.  It runs
+// the same number of CTAs per SM (so the same plan) with blocks of 3/4 BS
+// threads, which leaves it 85 registers a thread instead of 64: at 64 its
+// bookkeeping spilled registers out of the substep loops (16 x 32^3 x 4
+// FP32, 100 sweeps without any measurement work: 32.9 against the plain
+// kernel's 42.0 G updates/s).
+template <int BS, bool MEAS> struct BatchBlock { static constexpr int value = MEAS ? BS * 3 / 4 : BS; };
+
+template <int P, int BS, bool MEAS>
+__global__ void __launch_bounds__(BatchBlock<BS, MEAS>::value, (P == kF64 ? 512 : 1024) / BS)
     k_batch_groups(const BatchLattice* __restrict__ desc, const int* __restrict__ order,
                    const int4* __restrict__ plan, const int* __restrict__ cta_group, int nsweeps, int nor,
                    const uint32_t* sweep_base, const __grid_constant__ HBParams hp, GroupBarrier* bars, BatchCtl* ctl,
-                   unsigned long long timeout_ns) {
+                   unsigned long long timeout_ns, double* mhist, double* mpart, int nlat) {
   using R = typename Real<P>::T;
-  __shared__ BDeferred<R> queue[BatchQueue<BS>::value];
+  constexpr int kB = BatchBlock<BS, MEAS>::value;  // threads per CTA
+  // the deferral queue, sized for the larger (plaquette-carrying) entries
+  __shared__ __align__(16) unsigned char queue[BatchQueue<kB>::value * sizeof(Deferred<R, MEAS>)];
   __shared__ int qn;
+  PlainAcc<R> ps, pt;  // measured sweep: spatial and space-time plaquette sums
   const int group = cta_group[blockIdx.x];
   if (group < 0) return;
   // plan[group] = (first lattice in `order`, lattices, first CTA, CTAs)
@@ -208,14 +258,14 @@ __global__ void __launch_bounds__(BS, (P == kF64 ? 512 : 1024) / BS)
     const R beta = (R)desc[l].beta;
     const uint32_t tag = (uint32_t)mu | ((uint32_t)l << 2);
     switch (2 * mu + p) {
-      case 0: batch_substep<P, 0, 0, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 1: batch_substep<P, 0, 1, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 2: batch_substep<P, 1, 0, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 3: batch_substep<P, 1, 1, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 4: batch_substep<P, 2, 0, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 5: batch_substep<P, 2, 1, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      case 6: batch_substep<P, 3, 0, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
-      default: batch_substep<P, 3, 1, BS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn); break;
+      case 0: batch_substep<P, 0, 0, kB, false>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn, ps); break;
+      case 1: batch_substep<P, 0, 1, kB, false>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn, ps); break;
+      case 2: batch_substep<P, 1, 0, kB, false>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn, ps); break;
+      case 3: batch_substep<P, 1, 1, kB, MEAS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn, ps); break;
+      case 4: batch_substep<P, 2, 0, kB, false>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn, ps); break;
+      case 5: batch_substep<P, 2, 1, kB, MEAS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn, ps); break;
+      case 6: batch_substep<P, 3, 0, kB, false>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn, pt); break;
+      default: batch_substep<P, 3, 1, kB, MEAS>(L, g, rank, cpg, sweep, tag, beta, hp, queue, &qn, pt); break;
     }
   };
   // one lattice at a time, a barrier after each substep: the lattice's links
@@ -228,30 +278,74 @@ __global__ void __launch_bounds__(BS, (P == kF64 ? 512 : 1024) / BS)
     Links<P, kClassOff> L;
     L.set(desc[l].links, g.vh);
     switch (2 * mu + p) {
-      case 0: batch_or_substep<P, 0, 0, BS>(L, g, rank, cpg); break;
-      case 1: batch_or_substep<P, 0, 1, BS>(L, g, rank, cpg); break;
-      case 2: batch_or_substep<P, 1, 0, BS>(L, g, rank, cpg); break;
-      case 3: batch_or_substep<P, 1, 1, BS>(L, g, rank, cpg); break;
-      case 4: batch_or_substep<P, 2, 0, BS>(L, g, rank, cpg); break;
-      case 5: batch_or_substep<P, 2, 1, BS>(L, g, rank, cpg); break;
-      case 6: batch_or_substep<P, 3, 0, BS>(L, g, rank, cpg); break;
-      default: batch_or_substep<P, 3, 1, BS>(L, g, rank, cpg); break;
+      case 0: batch_or_substep<P, 0, 0, kB>(L, g, rank, cpg); break;
+      case 1: batch_or_substep<P, 0, 1, kB>(L, g, rank, cpg); break;
+      case 2: batch_or_substep<P, 1, 0, kB>(L, g, rank, cpg); break;
+      case 3: batch_or_substep<P, 1, 1, kB>(L, g, rank, cpg); break;
+      case 4: batch_or_substep<P, 2, 0, kB>(L, g, rank, cpg); break;
+      case 5: batch_or_substep<P, 2, 1, kB>(L, g, rank, cpg); break;
+      case 6: batch_or_substep<P, 3, 0, kB>(L, g, rank, cpg); break;
+      default: batch_or_substep<P, 3, 1, kB>(L, g, rank, cpg); break;
     }
   };
-  for (int li = 0; li < pl.y; ++li)
+  // measured sweeps: after the first substep of sweep sw (sw >= 1), the
+  // history entry of sweep sw - 1
+  auto after_first = [&](int l, int sw) {
+    if constexpr (MEAS) {
+      if (sw > 0 && rank == 0 && threadIdx.x < 32)
+        batch_history(mpart, pl.z, cpg, desc[l].g, mhist + ((size_t)(sw - 1) * nlat + l) * 4);
+    }
+  };
+  auto polyakov_part = [&](int l) {
+    const Geom g = desc[l].g;
+    Links<P, kClassOff> L;
+    L.set(desc[l].links, g.vh);
+    batch_polyakov_part<P, kB>(L, g, rank, cpg, mpart);
+  };
+  for (int li = 0; li < pl.y; ++li) {
+    const int l = order[pl.x + li];
     for (int sw = 0; sw < nsweeps; ++sw) {
+      bool first = true;
       for (int k = 0; k < nor; ++k)
         for (int mu = 0; mu < 4; ++mu)
           for (int p = 0; p < 2; ++p) {
-            or_substep(order[pl.x + li], mu, p);
+            or_substep(l, mu, p);
+            if constexpr (MEAS) {
+              if (first && sw > 0) polyakov_part(l);
+            }
             if (!group_barrier(bars + group, (unsigned)cpg, ctl, timeout_ns)) return;
+            if (first) after_first(l, sw);
+            first = false;
           }
       for (int mu = 0; mu < 4; ++mu)
         for (int p = 0; p < 2; ++p) {
-          substep(order[pl.x + li], sweep0 + (uint32_t)sw, mu, p);
+          substep(l, sweep0 + (uint32_t)sw, mu, p);
+          if constexpr (MEAS) {
+            if (first && sw > 0) polyakov_part(l);
+            if (mu == 3 && p == 1) {
+              // the sweep's plaquette sums of this CTA
+              block_sums_to<kB>(ps.value(), pt.value(), mpart + 4 * (size_t)blockIdx.x,
+                                mpart + 4 * (size_t)blockIdx.x + 1);
+              ps = PlainAcc<R>();
+              pt = PlainAcc<R>();
+            }
+          }
           if (!group_barrier(bars + group, (unsigned)cpg, ctl, timeout_ns)) return;
+          if (first) after_first(l, sw);
+          first = false;
         }
     }
+    if constexpr (MEAS) {
+      // the lattice's last sweep of this call
+      if (nsweeps > 0) {
+        polyakov_part(l);
+        if (!group_barrier(bars + group, (unsigned)cpg, ctl, timeout_ns)) return;
+        after_first(l, nsweeps);
+        // the next lattice's first substep overwrites these CTA sums only
+        // after a barrier that warp 0 of the first CTA reaches after reading them
+      }
+    }
+  }
 }
 
 }  // namespace su2
@@ -279,6 +373,7 @@ struct su2_batch {
   Scratch scratch;
   double* d_results;
   double* h_results;
+  double* d_mpart;  // measured sweeps: four partial-sum slots per CTA
   cudaStream_t stream;
   bool own_stream;
   cudaStream_t cap_stream;
@@ -302,7 +397,11 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 template <int P, int BS> int occupancy_blocks() {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_groups<P, BS>, BS, 0);
+  int per_sm_meas = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_groups<P, BS, false>, BS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_meas, k_batch_groups<P, BS, true>,
+                                                BatchBlock<BS, true>::value, 0);
+  if (per_sm_meas < per_sm) per_sm = per_sm_meas;
   return per_sm;
 }
 
@@ -423,12 +522,13 @@ int set_groups(su2_batch* b, int G) {
   return SU2_OK;
 }
 
-cudaError_t launch_groups(const su2_batch* b, const BatchLattice* d_desc, int n, cudaStream_t st) {
+cudaError_t launch_groups(const su2_batch* b, const BatchLattice* d_desc, int n, cudaStream_t st,
+                          double* mhist = nullptr) {
   const HBParams hp = batch_hp(b);
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof cfg);
   cfg.gridDim = dim3(b->grid);
-  cfg.blockDim = dim3(b->bs);
+  cfg.blockDim = dim3(mhist ? b->bs * 3 / 4 : b->bs);   // BatchBlock
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -439,15 +539,18 @@ cudaError_t launch_groups(const su2_batch* b, const BatchLattice* d_desc, int n,
   cudaError_t e;
   auto go = [&](auto kernel) {
     return cudaLaunchKernelEx(&cfg, kernel, d_desc, (const int*)b->d_order, (const int4*)b->d_plan,
-                              (const int*)b->d_cta_group, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns);
+                              (const int*)b->d_cta_group, n, b->nor, sw, hp, b->d_bars, b->d_ctl, b->timeout_ns,
+                              mhist, b->d_mpart, b->n);
   };
-  if (b->bs == 512) {
-    e = b->prec == kF64 ? go(k_batch_groups<kF64, 512>)
-                        : b->prec == kF32 ? go(k_batch_groups<kF32, 512>) : go(k_batch_groups<kF16Q, 512>);
-  } else {
-    e = b->prec == kF64 ? go(k_batch_groups<kF64, 256>)
-                        : b->prec == kF32 ? go(k_batch_groups<kF32, 256>) : go(k_batch_groups<kF16Q, 256>);
-  }
+  auto by_bs = [&](auto meas) {
+    constexpr bool M = decltype(meas)::value;
+    if (b->bs == 512)
+      return b->prec == kF64 ? go(k_batch_groups<kF64, 512, M>)
+                             : b->prec == kF32 ? go(k_batch_groups<kF32, 512, M>) : go(k_batch_groups<kF16Q, 512, M>);
+    return b->prec == kF64 ? go(k_batch_groups<kF64, 256, M>)
+                           : b->prec == kF32 ? go(k_batch_groups<kF32, 256, M>) : go(k_batch_groups<kF16Q, 256, M>);
+  };
+  e = mhist ? by_bs(std::true_type{}) : by_bs(std::false_type{});
   if (e == cudaSuccess) count_launches(1);
   return e;
 }
@@ -533,6 +636,7 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   const size_t o_cnt = o; o = align256(o + 64 * sizeof(unsigned int));
   const size_t o_out = o; o = align256(o + kScratchOut * sizeof(double));
   const size_t o_res = o; o = align256(o + 3 * (size_t)n * sizeof(double));
+  const size_t o_mpart = o; o = align256(o + 4 * (size_t)kMaxCtas * sizeof(double));
   cudaError_t e = cudaMalloc(&b->base, o);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -552,6 +656,7 @@ extern "C" int su2_batch_init(su2_batch** out, int n, const int* dims, const dou
   b->scratch.counter = (unsigned int*)(base + o_cnt);
   b->scratch.out = (double*)(base + o_out);
   b->d_results = (double*)(base + o_res);
+  b->d_mpart = (double*)(base + o_mpart);
   if (cuda_stream) {
     b->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -697,6 +802,35 @@ extern "C" int su2_batch_sweep(su2_batch* b, int n) {
   b->sweep += (uint64_t)n;
   // a timed-out barrier is reported by the call that ran it
   return check_ctl(b, before);
+}
+
+extern "C" int su2_batch_sweep_measure(su2_batch* b, int n, double* hist) {
+  clear_error();
+  if (!b) return fail(SU2_EINVAL, "handle is NULL");
+  if (n < 1) return fail(SU2_EINVAL, "n must be >= 1");
+  if (!hist) return fail(SU2_EINVAL, "hist is NULL");
+  if (b->sweep + (uint64_t)n >= 0xFFFFFFFFull) return fail(SU2_EINVAL, "sweep counter would reach the reserved index 2^32 - 1");
+  DeviceGuard dg(b->device);
+  const size_t bytes = (size_t)n * b->n * 4 * sizeof(double);
+  double* d_hist = nullptr;
+  SU2_CU(cudaMallocAsync(&d_hist, bytes, b->stream));
+  const uint64_t before = b->sweep;
+  cudaError_t e = launch_groups(b, b->d_desc, n, b->stream, d_hist);
+  if (e == cudaSuccess) e = launch_add_u32(b->d_sweep, (uint32_t)n, b->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(d_hist, b->stream);
+    cudaStreamSynchronize(b->stream);
+    return fail(SU2_ECUDA, "batched measured sweep launch failed: %s", cudaGetErrorString(e));
+  }
+  b->sweep += (uint64_t)n;
+  const int rc = check_ctl(b, before);
+  if (rc == SU2_OK) e = cudaMemcpyAsync(hist, d_hist, bytes, cudaMemcpyDeviceToHost, b->stream);
+  cudaFreeAsync(d_hist, b->stream);
+  const cudaError_t e2 = cudaStreamSynchronize(b->stream);
+  if (rc != SU2_OK) return rc;
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(SU2_ECUDA, "batched measured sweep: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  return SU2_OK;
 }
 
 extern "C" int su2_batch_tune(su2_batch* b, int sweeps, int* groups) {

@@ -1,6 +1,7 @@
 // One link's heat-bath update (Section 2, Eqs. 5-9, 11), shared by the
-// substep kernel (su2_heatbath.cu) and the fused parity-pair kernel
-// (su2_pair.cu), so both run the same arithmetic and leave the same links.
+// substep kernel (su2_heatbath.cu), the fused parity-pair kernel
+// (su2_pair.cu) and the batched kernel (su2_batch.cu), so all of them run
+// the same arithmetic and leave the same links.
 // Paper: Cardoso & Bicudo, arXiv:1010.4834.
 //
 // Every lane makes the link's first a0 trial inline.  A link that rejects it
@@ -61,8 +62,9 @@ __device__ __forceinline__ int finish_deferred(const Deferred<R, MEAS>& d, uint4
 // Update link h of class (MU, PAR).  Rejected first trials go to queue slot
 // atomicAdd(qn, 1) when it is below CAP.  MCG: the staple's loads of the
 // other-parity MU class bypass L1 (the fused pair kernel writes that class
-// earlier in the same launch).
-template <int P, int MU, bool MEAS, int PAR, bool MCG, int CAP, int CP>
+// earlier in the same launch).  NC: read-only loads; the persistent batched
+// kernel, whose other CTAs write links during the launch, loads coherently.
+template <int P, int MU, bool MEAS, int PAR, bool MCG, int CAP, int CP, bool NC = true>
 __device__ __forceinline__ void hb_link(const Links<P, CP>& L, const Geom& g, int h, uint32_t tag, uint32_t sweep,
                                         typename Real<P>::T beta, const HBParams& hp,
                                         Deferred<typename Real<P>::T, MEAS>* queue, int* qn,
@@ -74,8 +76,8 @@ __device__ __forceinline__ void hb_link(const Links<P, CP>& L, const Geom& g, in
   const Site x = site_from_half(g, (uint32_t)h, p);
   Quat<R> lower;
   Quat<R> sig;
-  if constexpr (MEAS) sig = staple_split<P, MU, true, CP, MCG>(L, g, x, h, p, lower);
-  else sig = staple<P, MU, 0xF, true, CP, MCG>(L, g, x, h, p);
+  if constexpr (MEAS) sig = staple_split<P, MU, NC, CP, MCG>(L, g, x, h, p, lower);
+  else sig = staple<P, MU, 0xF, NC, CP, MCG>(L, g, x, h, p);
   const uint32_t site = philox_site(g, x);
   const uint4 ctr = make_uint4(site, tag, sweep, 0u);
   const R k2 = qdot(sig, sig);
@@ -113,20 +115,20 @@ __device__ __forceinline__ void hb_link(const Links<P, CP>& L, const Geom& g, in
     } else {
       Quat<R> nl;
       const int n = finish_deferred<R, MEAS>(d, ctr, hp, &nl);
-      if constexpr (MEAS) plaq.add(qdot(n ? L.put(2 * MU + p, h, nl) : L.ld(2 * MU + p, h), lower));
+      if constexpr (MEAS) plaq.add(qdot(n ? L.put(2 * MU + p, h, nl) : ldl<P, NC>(L, 2 * MU + p, h), lower));
       else if (n) L.st(2 * MU + p, h, nl);
       cnt.trials += n ? (unsigned)n : (unsigned)hp.max_tries;
       cnt.capped += n == 0;
     }
   } else {
-    if constexpr (MEAS) plaq.add(qdot(L.ld(2 * MU + p, h), lower));
+    if constexpr (MEAS) plaq.add(qdot(ldl<P, NC>(L, 2 * MU + p, h), lower));
     cnt.trials += 1;
     cnt.capped += 1;
   }
 }
 
 // Finish the queue entries i = threadIdx.x, threadIdx.x + blockDim.x, ... < n.
-template <int P, int MU, bool MEAS, int PAR, int CP>
+template <int P, int MU, bool MEAS, int PAR, int CP, bool NC = true>
 __device__ __forceinline__ void hb_drain(const Links<P, CP>& L, const Deferred<typename Real<P>::T, MEAS>* queue, int n,
                                          uint32_t tag, uint32_t sweep, const HBParams& hp,
                                          PlainAcc<typename Real<P>::T>& plaq, HBCount& cnt) {
@@ -136,7 +138,7 @@ __device__ __forceinline__ void hb_drain(const Links<P, CP>& L, const Deferred<t
     const Deferred<R, MEAS> d = queue[i];
     Quat<R> nl;
     const int t = finish_deferred<R, MEAS>(d, make_uint4(d.site, tag, sweep, 0u), hp, &nl);
-    if constexpr (MEAS) plaq.add(qdot(t ? L.put(2 * MU + p, d.h, nl) : L.ld(2 * MU + p, d.h), d.lower));
+    if constexpr (MEAS) plaq.add(qdot(t ? L.put(2 * MU + p, d.h, nl) : ldl<P, NC>(L, 2 * MU + p, d.h), d.lower));
     else if (t) L.st(2 * MU + p, d.h, nl);
     cnt.trials += t ? (unsigned)t : (unsigned)hp.max_tries;
     cnt.capped += t == 0;

@@ -291,6 +291,14 @@ class Batch:
     def sweep(self, n=1):
         check(_lib.load().su2_batch_sweep(self._h, int(n)))
 
+    def sweep_measure(self, n):
+        """n sweeps, each followed by every lattice's plaquette (all,
+        spatial, space-time) and Polyakov loop: an (n, lattices, 4) array
+        (su2_batch_sweep_measure)."""
+        out = np.empty((int(n), self.n, 4))
+        check(_lib.load().su2_batch_sweep_measure(self._h, int(n), _dptr(out)))
+        return out
+
     @property
     def groups(self):
         g = C.c_int()

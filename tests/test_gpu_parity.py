@@ -461,6 +461,46 @@ def test_batched_sweep_parity(prec):
     b.close()
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16q"])
+def test_batched_measured_sweeps_against_the_oracle(prec):
+    # every sweep's plaquette and Polyakov loop of every lattice against the
+    # oracle's measurements of the same links (a twin batch swept one sweep
+    # at a time; the chain itself is compared with the oracle in
+    # test_batched_sweep_parity), with one group per lattice and with one
+    # group for all; the 16^3 x 8 lattice's group spans many CTAs
+    dims = [(4, 4, 4, 4), (6, 4, 4, 2), (16, 16, 16, 8), (2, 4, 6, 4)]
+    betas = [2.0, 2.5, 2.3, 0.0]
+    b = Batch(dims, betas, seed=17, start="hot", prec=prec)
+    twin = Batch(dims, betas, seed=17, start="hot", prec=prec)
+    for G in (len(dims), 1):
+        b.groups = G
+        hist = b.sweep_measure(3)
+        assert hist.shape == (3, len(dims), 4)
+        for sw in range(3):
+            twin.sweep(1)
+            for i, d in enumerate(dims):
+                U = twin.get_links(i)
+                ref = list(oracle.plaquette(list(d), U)) + [oracle.polyakov(list(d), U)]
+                np.testing.assert_allclose(hist[sw, i], ref, atol=MTOL[prec], rtol=0)
+        for i in range(len(dims)):
+            assert np.array_equal(b.get_links(i), twin.get_links(i))   # measuring leaves the chain alone
+    b.close()
+    twin.close()
+
+
+def test_batched_measured_sweep_matches_the_single_lattice_history():
+    # lattice i of a batch is the single-lattice chain with lattice_id i; for
+    # lattice 0 (lattice_id 0) the batched history equals su2_sweep_measure's
+    dims = [(8, 8, 8, 8), (4, 4, 4, 8)]
+    b = Batch(dims, [2.4, 2.2], seed=5, start="hot", prec="f64")
+    hist = b.sweep_measure(4)
+    lat = Lattice(dims[0], 2.4, seed=5, start="hot", prec="f64")
+    ref = lat.sweep_measure(4)
+    np.testing.assert_allclose(hist[:, 0, :], ref, atol=1e-12, rtol=0)
+    lat.close()
+    b.close()
+
+
 def test_batched_rejects_a_member_beyond_32_bit_offsets():
     # 512^3 x 8 = 2^30 sites (a valid single lattice): the batched kernel's
     # 32-bit link offsets do not reach it; rejected before anything is allocated
