@@ -483,6 +483,15 @@ void make_plan(const su2_batch* b, int G, std::vector<int>& order, std::vector<i
     return a.first > c.first;
   });
   for (size_t k = 0; k < frac.size() && used < ctas; ++k, ++used) share[frac[k].second] += 1;
+  // no group gets more CTAs than its largest lattice has links for at the
+  // smallest block (192 threads: the measured kernel's 3/4 of 256), so that a
+  // small lattice alone does not spread its barriers over idle CTAs; CTAs
+  // left over have no group and leave at once
+  for (int gi = 0; gi < G; ++gi) {
+    int64_t mx = 1;
+    for (int i : members[gi]) mx = std::max<int64_t>(mx, b->desc[i].g.vh);
+    share[gi] = (int)std::min<int64_t>(share[gi], std::max<int64_t>(1, (mx + 191) / 192));
+  }
   order.clear();
   plan.assign(G, make_int4(0, 0, 0, 0));
   cta_group.assign(b->grid, -1);
