@@ -164,15 +164,6 @@ def small_configs(torch):
     t = timed(lambda: lat.sweep_measure(100))
     out["8^4_f64_cold_100sweeps_measured"] = 100 * 4 * 8 ** 4 / t
     lat.close()
-    # the same run as a batch of one lattice: one persistent launch, a barrier
-    # among a few CTAs per substep instead of a kernel launch
-    bat = Batch([(8, 8, 8, 8)], [2.4], seed=1, start="cold", prec="f64")
-    bat.sweep_measure(16)
-    bat.close()
-    bat = Batch([(8, 8, 8, 8)], [2.4], seed=1, start="cold", prec="f64")
-    t = timed(lambda: bat.sweep_measure(100))
-    out["8^4_f64_cold_100sweeps_measured_batched"] = 100 * 4 * 8 ** 4 / t
-    bat.close()
     # 16^4, beta 2.5, hot, FP32: 500 sweeps, then 25 APE steps and W(R,T <= 8)
     lat = Lattice((16, 16, 16, 16), 2.5, seed=1, start="hot", prec="f32")
 
