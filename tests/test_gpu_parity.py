@@ -275,21 +275,24 @@ def test_measurements_on_thermalised_configuration():
 
 # Wilson loops across the kernels' chunk boundaries: R beyond one register
 # chunk (R = 17 needs a second chunk that starts from prefix products), a
-# partly used 16-wide R chunk, T beyond one 16-wide T chunk, and planes with
-# fewer than 32 sites per row (loops wrap several times around a row).
+# partly used 16-wide R chunk (R = 12; R = 16 at T = 4 fills one), T beyond
+# one 16-wide T chunk, and planes with fewer than 32 sites per row (loops
+# wrap several times around a row).
 _WILSON_REF = {}
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16q", "f64"])
 @pytest.mark.parametrize("dims,rmax,tmax", [((18, 18, 18, 4), 17, 4), ((12, 12, 12, 4), 12, 4),
                                             ((4, 4, 4, 18), 4, 18), ((6, 10, 8, 6), 6, 6),
+                                            ((16, 16, 16, 8), 16, 4),
                                             # 64-site rows with 96 slices: planes too large for
                                             # shared memory, so work units are bands of time
                                             # slices (76 / 60 slices in FP32, 30 / 14 in FP64)
                                             ((64, 2, 2, 96), 2, 16), ((64, 2, 2, 96), 2, 20),
-                                            # 432-site rows: not even one time slice (plus the
-                                            # lines' overhang) fits, the global-memory kernel runs
-                                            ((432, 2, 2, 16), 2, 16)])
+                                            # 432- and 480-site rows: not even one time slice
+                                            # (plus the lines' overhang) fits, the global-memory
+                                            # kernel runs
+                                            ((432, 2, 2, 16), 2, 16), ((480, 2, 2, 16), 2, 16)])
 def test_wilson_loops_across_chunks(dims, rmax, tmax, prec):
     U = inputs.random_field(dims, 23)
     ref = as_stored(U, prec)
@@ -300,6 +303,23 @@ def test_wilson_loops_across_chunks(dims, rmax, tmax, prec):
     lat.set_links(U)
     np.testing.assert_allclose(lat.wilson_loops(rmax, tmax), _WILSON_REF[key], atol=MTOL[prec] * 5, rtol=0)
     lat.close()
+
+
+def test_wilson_full_chunks_fp32_f16q_against_fp64_kernel():
+    # W(16,16) on 32^4, the benchmark's loop range: one full 16 x 16 chunk of
+    # the FP32 / F16Q time-outer kernel against the FP64 kernel's two 8-wide
+    # R chunks (pinned to the oracle above), on the same stored links
+    dims = (32, 32, 32, 32)
+    U = inputs.random_field(dims, 37)
+    b = Lattice(dims, 2.0, prec="f64")
+    for prec in ("f32", "f16q"):
+        b.set_links(as_stored(U, prec))
+        ref = b.wilson_loops(16, 16)
+        a = Lattice(dims, 2.0, prec=prec)
+        a.set_links(U)
+        np.testing.assert_allclose(a.wilson_loops(16, 16), ref, atol=1e-5, rtol=0)
+        a.close()
+    b.close()
 
 
 def test_wilson_loops_both_chunkings_fp32_against_fp64_kernel():
