@@ -10,6 +10,7 @@
 // kernels: per-thread sums (compensated when the arithmetic is FP32), FP64
 // warp shuffles, one partial per block and a last-block finisher that adds
 // the partials in a fixed order, so a result is reproducible run to run.
+#include <algorithm>
 #include <atomic>
 #include <cfloat>
 #include <mutex>
@@ -699,6 +700,206 @@ __global__ void __launch_bounds__(kThreads) k_wilson_rt_final(const double* part
   if (threadIdx.x == 0) out[o] = tot * inv;
 }
 
+// ---------------------------------------------------------------------------
+// Wilson loops in temporal gauge.  The loop of Eq. 18 is gauge invariant, so
+// it may be evaluated on any gauge transform U'_mu(x) = G(x) U_mu(x)
+// G(x+mu)^dag of the links.  In the (MU, time) plane with coordinates (a, t)
+// take G(a, 0) = 1 and G(a, t+1) = G(a, t) U_t(a, t) (each product
+// normalised, so G stays a unit quaternion): every time line then becomes
+// T_T(a, t) = G(a,t)^dag G(a,t+T), and the loop at (a, t) becomes
+//   W = (1/2) Tr[S'_R(a,t) S'_R(a,t+T)^dag] = S'_R(a,t) . S'_R(a,t+T),
+// with S'_R(a, r) = U'(a, r) U'(a+1, r) ... U'(a+R-1, r) the spatial line of
+// the transformed links (the G between neighbouring links cancel).  A time
+// line that wraps past the last slice is G(a,t)^dag P(a) G(a,t') with P(a) =
+// G(a, Nt) the Polyakov line, so rows Nt + t' of an extended plane hold
+// U'(a, Nt + t') = P(a) U'(a, t') P(a+1)^dag and no loop needs a wrap test.
+// Per loop that is one dot product (4 FMA) where the direct form needs two
+// quaternion products and a dot (36 FMA); the lines cost one product per
+// (site, R), shared by all T.
+//
+// One block per plane at a time: the time links are scanned in chunks of
+// kTgRows slices (local products, then a prefix over the chunks), the
+// transformed spatial links U' of the extended plane are staged in shared
+// memory, then for R = 1 .. rmax every thread extends the lines of its
+// kTgRows rows of one column a by one link, publishes them, and adds the
+// dot products with the lines kTgT rows ahead into registers acc[T]; a
+// transposing warp reduction per R folds them into the block's FP64 totals
+// in a fixed order.  Per-block sums go to `partials` in the layout
+// k_wilson_rt_final reads (one 16 x 16 chunk).
+// ---------------------------------------------------------------------------
+#ifndef SU2_WILSON_TG
+#define SU2_WILSON_TG 1
+#endif
+constexpr int kTgRows = 8;   // time slices (rows) a thread owns
+constexpr int kTgT = 16;     // T values in registers; also the rows added past Nt
+template <int P> struct TgThreads { static constexpr int value = P == kF64 ? 384 : 640; };
+
+template <class R> __device__ __forceinline__ Quat<R> qunit(const Quat<R>& q) {
+  return qscale(q, Math<R>::rsqrt(qdot(q, q)));
+}
+
+// Site (column a, slice t) of the plane (mu, c1, c2).
+__device__ __forceinline__ Site plane_site(const Geom& g, int mu, int a, int c1, int c2, int t) {
+  Site y;
+  y.x0 = mu == 0 ? a : c1;
+  y.x1 = mu == 0 ? c1 : (mu == 1 ? a : c2);
+  y.x2 = mu == 2 ? a : c2;
+  y.x3 = t;
+  y.row = y.x1 + g.n[1] * (y.x2 + g.n[2] * y.x3);
+  return y;
+}
+
+template <int P>
+__global__ void __launch_bounds__(TgThreads<P>::value, 1)
+    k_wilson_tg(Links<P> Ls, Links<P> Lt, Geom g, int rmax, int tmax, double* partials) {
+  using R = typename Real<P>::T;
+  constexpr int NTH = TgThreads<P>::value, ROWS = kTgRows;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double acc64[16 * kTgT];  // block totals; slot (R-1) kTgT + T-1
+  __shared__ R wsum[NTH / 32][kTgT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nt = g.n[3], nr = nt + kTgT;
+  const int nchunks = (nr + ROWS - 1) / ROWS, nscan = (nt + ROWS - 1) / ROWS;
+  const int hts = g.n0h * g.st[3];
+  for (int i = threadIdx.x; i < 16 * kTgT; i += blockDim.x) acc64[i] = 0.0;
+  const int ntr0 = g.n[1] * g.n[2], ntr1 = g.n[0] * g.n[2], ntr2 = g.n[0] * g.n[1];
+  const int nunits = ntr0 + ntr1 + ntr2;
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int mu = u < ntr0 ? 0 : (u < ntr0 + ntr1 ? 1 : 2);
+    const int tr = u - (mu == 0 ? 0 : (mu == 1 ? ntr0 : ntr0 + ntr1));
+    const int nm = mu == 0 ? g.n[0] : (mu == 1 ? g.n[1] : g.n[2]);
+    const int n1st = mu == 0 ? g.n[1] : g.n[0];
+    const int c1 = tr % n1st, c2 = tr / n1st;
+    const int W = nm + rmax - 1;  // columns of the staged plane (column c is plane column c mod nm)
+    Quat<R>* Ue = reinterpret_cast<Quat<R>*>(smem_raw);  // Ue[r W + c] = U'(c, r), r < nr
+    Quat<R>* Sb = Ue + nr * W;                           // Sb[r nm + a]: G(a, r), then the lines S'_R(a, r)
+    Quat<R>* Ct = Sb + nr * nm;                          // Ct[k nm + a]: product of scan chunk k
+    Quat<R>* Pb = Ct + nscan * nm;                       // Pb[a] = P(a)
+    const int item = threadIdx.x;
+    const int a = item % nm, c = item / nm;
+    const bool active = c < nchunks;
+    const int r0 = c * ROWS;
+    __syncthreads();  // the previous plane's readers are done
+    // (1) time links of this thread's rows: products within the chunk
+    if (active && r0 < nt) {
+      const Site y = plane_site(g, mu, a, c1, c2, r0);
+      int h = hidx(g, y), par = parity(y);
+      Quat<R> L = qone<R>();
+#pragma unroll
+      for (int i = 0; i < ROWS; ++i) {
+        if (r0 + i < nt) {
+          Sb[(r0 + i) * nm + a] = L;
+          L = qunit(qmul(L, Lt.ld(6 + par, h)));
+          h += hts;
+          par ^= 1;
+        }
+      }
+      Ct[c * nm + a] = L;
+    }
+    __syncthreads();
+    // (2) prefix over the chunks: G(a, r) for the thread's rows, P(a) = G(a, Nt)
+    if (active && r0 < nt) {
+      Quat<R> Q = qone<R>();
+      for (int k = 0; k < c; ++k) Q = qunit(qmul(Q, Ct[k * nm + a]));
+      if (c > 0) {
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i)
+          if (r0 + i < nt) Sb[(r0 + i) * nm + a] = qunit(qmul(Q, Sb[(r0 + i) * nm + a]));
+      }
+      if (c == nscan - 1) Pb[a] = qunit(qmul(Q, Ct[c * nm + a]));
+    }
+    __syncthreads();
+    // (3) U'(c, r) = G(c, t) U_mu(c, t) G(c+1, t)^dag, conjugated by P on the extended rows
+    for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
+      const int cc = i % W, r = i / W;
+      const int aa = cc % nm, an = aa + 1 == nm ? 0 : aa + 1;
+      const bool ext = r >= nt;
+      const int t = ext ? (r - nt) % nt : r;
+      const Site y = plane_site(g, mu, aa, c1, c2, t);
+      const Quat<R> lnk = Ls.ld(2 * mu + parity(y), hidx(g, y));
+      Quat<R> v = qmul_nd(qmul(Sb[t * nm + aa], lnk), Sb[t * nm + an]);
+      if (ext) v = qmul_nd(qmul(Pb[aa], v), Pb[an]);
+      Ue[r * W + cc] = v;
+    }
+    __syncthreads();  // Sb now holds lines
+    // (4) R = 1 .. rmax
+    const int norig = active ? min(max(nt - r0, 0), ROWS) : 0;  // rows of this thread that start loops
+    Quat<R> own[ROWS];
+    R acc[kTgT];
+#pragma unroll
+    for (int k = 0; k < kTgT; ++k) acc[k] = R(0);
+    for (int Rl = 1; Rl <= rmax; ++Rl) {
+      if (active) {
+#pragma unroll
+        for (int i = 0; i < ROWS; ++i) {
+          if (r0 + i < nr) {
+            const Quat<R> v = Ue[(r0 + i) * W + a + Rl - 1];
+            own[i] = Rl == 1 ? v : qmul(own[i], v);
+            Sb[(r0 + i) * nm + a] = own[i];
+          }
+        }
+      }
+      __syncthreads();
+      if (norig == ROWS) {
+        // every row of the thread starts loops: rows r0 + 1 .. r0 + ROWS - 1 + kTgT
+#pragma unroll
+        for (int j = 1; j < ROWS + kTgT; ++j) {
+          const Quat<R> w = j < ROWS ? own[j < ROWS ? j : 0] : Sb[(r0 + j) * nm + a];
+#pragma unroll
+          for (int i = 0; i < ROWS; ++i) {
+            const int T = j - i;
+            if (T >= 1 && T <= kTgT && T <= tmax)
+              acc[T - 1] = fma(own[i].w, w.w, fma(own[i].x, w.x, fma(own[i].y, w.y, fma(own[i].z, w.z, acc[T - 1]))));
+          }
+        }
+      } else if (norig > 0) {
+        // the chunk that holds slice Nt - 1: rows norig .. ROWS - 1 start no loops
+#pragma unroll
+        for (int j = 1; j < ROWS + kTgT; ++j) {
+          if (j - kTgT < norig) {
+            const Quat<R> w = j < ROWS ? own[j < ROWS ? j : 0] : Sb[(r0 + j) * nm + a];
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+              const int T = j - i;
+              if (T >= 1 && T <= kTgT && T <= tmax && i < norig)
+                acc[T - 1] = fma(own[i].w, w.w, fma(own[i].x, w.x, fma(own[i].y, w.y, fma(own[i].z, w.z, acc[T - 1]))));
+            }
+          }
+        }
+      }
+      // this R's sums: a transposing butterfly leaves lanes 2k and 2k+1 the
+      // warp total of slot lo; the even lanes write it, 16 threads fold
+      int lo = 0;
+#pragma unroll
+      for (int lev = 0; lev < 4; ++lev) {
+        const int off = 16 >> lev, half = 8 >> lev;
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          if (m < half) {
+            const R send = upper ? acc[m] : acc[m + half];
+            const R keep = upper ? acc[m + half] : acc[m];
+            acc[m] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+          }
+        }
+        if (upper) lo += half;
+      }
+      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+      if ((lane & 1) == 0) wsum[warp][lo] = acc[0];
+#pragma unroll
+      for (int k = 0; k < kTgT; ++k) acc[k] = R(0);
+      __syncthreads();
+      if (threadIdx.x < kTgT) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)wsum[w][threadIdx.x];
+        acc64[(Rl - 1) * kTgT + threadIdx.x] += t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 16 * kTgT; i += blockDim.x) partials[(size_t)blockIdx.x * 16 * kTgT + i] = acc64[i];
+}
+
 // out[(R-1) tmax + (T-1)]: one block per output adds the per-block sums of the
 // three directions and all x-blocks of T's chunk, in a fixed order.
 template <int TC>
@@ -948,13 +1149,68 @@ static cudaError_t launch_wilson_rt(const LatticeView& v, const void* spatial, i
   return cudaErrorInvalidValue;
 }
 
+// The temporal-gauge kernel when R and T are at most 16, a plane's columns
+// times its row chunks fit one block, and the extended plane fits in shared
+// memory; *used = false otherwise.
+template <int P>
+static cudaError_t launch_wilson_tg(const LatticeView& v, const void* spatial, int rmax, int tmax,
+                                    const Scratch& s, cudaStream_t st, bool* used) {
+  using R = typename Real<P>::T;
+  constexpr int kMaxThreads = TgThreads<P>::value;
+  *used = false;
+  if (!SU2_WILSON_TG || rmax > 16 || tmax > kTgT) return cudaSuccess;
+  const int nmax = std::max(v.g.n[0], std::max(v.g.n[1], v.g.n[2]));
+  const int nt = v.g.n[3], nr = nt + kTgT;
+  const int nchunks = (nr + kTgRows - 1) / kTgRows, nscan = (nt + kTgRows - 1) / kTgRows;
+  const int nth = (nmax * nchunks + 31) / 32 * 32;
+  if (nth > kMaxThreads) return cudaSuccess;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_wilson_tg<P>);
+  if (e != cudaSuccess) return e;
+  const int64_t smem = ((int64_t)nr * (nmax + rmax - 1) + (int64_t)nr * nmax + (int64_t)nscan * nmax + nmax) *
+                       (int64_t)sizeof(Quat<R>);
+  const int64_t dyn_max = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
+  if (smem > dyn_max) return cudaSuccess;
+  static bool attr_set[64] = {false};
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    e = cudaFuncSetAttribute(k_wilson_tg<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson_tg<P>, nth, (size_t)smem);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t nunits = (int64_t)v.g.n[1] * v.g.n[2] + (int64_t)v.g.n[0] * v.g.n[2] + (int64_t)v.g.n[0] * v.g.n[1];
+  int64_t gx = (int64_t)device_info().sms * per_sm;
+  if (gx > nunits) gx = nunits;
+  const int64_t cap = (int64_t)kScratchPartials / (16 * kTgT);
+  if (gx > cap) gx = cap;
+  *used = true;
+  auto Lt = links_of<P>(v.links, v.g.vh);
+  auto Ls = links_of<P>(const_cast<void*>(spatial), v.g.vh);
+  k_wilson_tg<P><<<(unsigned)gx, nth, (size_t)smem, st>>>(Ls, Lt, v.g, rmax, tmax, s.partials);
+  count_launches(1);
+  const int64_t V = 2 * v.g.vh;
+  k_wilson_rt_final<16><<<rmax * tmax, kThreads, 0, st>>>(s.partials, (int)gx, 1, tmax, 1.0 / (3.0 * (double)V),
+                                                          s.out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_wilson(const LatticeView& v, const void* spatial, int rmax, int tmax,
                           const Scratch& s, cudaStream_t st) {
   if (rmax < 1 || rmax > kWilsonMaxR || tmax < 1) return cudaErrorInvalidValue;
   {
     bool used = false;
     cudaError_t e = cudaSuccess;
-    SU2_DISPATCH(v.prec, { e = launch_wilson_rt<P>(v, spatial, rmax, tmax, s, st, &used); });
+    SU2_DISPATCH(v.prec, {
+      e = launch_wilson_tg<P>(v, spatial, rmax, tmax, s, st, &used);
+      if (e == cudaSuccess && !used) e = launch_wilson_rt<P>(v, spatial, rmax, tmax, s, st, &used);
+    });
     if (e != cudaSuccess || used) return e;
   }
   // rows too long for even one time slice in shared memory: global-memory kernel

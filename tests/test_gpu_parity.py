@@ -273,11 +273,13 @@ def test_measurements_on_thermalised_configuration():
     lat.close()
 
 
-# Wilson loops across the kernels' chunk boundaries: R beyond one register
-# chunk (R = 17 needs a second chunk that starts from prefix products), a
-# partly used 16-wide R chunk (R = 12; R = 16 at T = 4 fills one), T beyond
-# one 16-wide T chunk, and planes with fewer than 32 sites per row (loops
-# wrap several times around a row).
+# Wilson loops across the kernels' limits: R and T up to 16 run the
+# temporal-gauge kernel (R = 12 and 16 here, planes that wrap a line several
+# times around a row); R = 17 or T > 16 the time-outer kernel (R = 17 needs
+# its second register chunk, which starts from prefix products; T = 18, 20 a
+# second T chunk); planes too large for one block of the temporal-gauge
+# kernel fall back to the time-outer kernel's bands or the global-memory
+# kernel.
 _WILSON_REF = {}
 
 
@@ -306,9 +308,10 @@ def test_wilson_loops_across_chunks(dims, rmax, tmax, prec):
 
 
 def test_wilson_full_chunks_fp32_f16q_against_fp64_kernel():
-    # W(16,16) on 32^4, the benchmark's loop range: one full 16 x 16 chunk of
-    # the FP32 / F16Q time-outer kernel against the FP64 kernel's two 8-wide
-    # R chunks (pinned to the oracle above), on the same stored links
+    # W(16,16) on 32^4, the benchmark's loop range (every R up to 16, every T
+    # up to 16, time lines wrapping past the last slice) in the temporal-gauge
+    # kernel: FP32 / F16Q against FP64 (pinned to the oracle above) on the
+    # same stored links
     dims = (32, 32, 32, 32)
     U = inputs.random_field(dims, 37)
     b = Lattice(dims, 2.0, prec="f64")
