@@ -190,7 +190,10 @@ int su2_restart(su2_lattice* h, int start);
  * of the call (one synchronisation per 1024 sweeps).  Advances the sweep
  * counter by n.  The plaquette is summed inside the sweep (in the
  * odd-parity substeps of mu = 1, 2, 3, from their staples), so it equals
- * su2_plaquette of the new configuration up to the order of summation; the
+ * su2_plaquette of the new configuration up to the order of summation (a
+ * link whose first a0 trial was rejected adds its term in whichever thread
+ * finishes it, which can change from run to run, so the plaquette can vary
+ * in its last bits, about 1e-11 on 64^4 FP32, while the links do not); the
  * Polyakov loop equals su2_polyakov; the links are the same as after
  * su2_heatbath_sweep.  A measured sweep is nine launches (eight substeps and
  * the Polyakov kernel, which also finishes the plaquette and advances the

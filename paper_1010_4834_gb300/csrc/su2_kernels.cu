@@ -809,7 +809,9 @@ __global__ void __launch_bounds__(TgThreads<P>::value, 1)
       if (c == nscan - 1) Pb[a] = qunit(qmul(Q, Ct[c * nm + a]));
     }
     __syncthreads();
-    // (3) U'(c, r) = G(c, t) U_mu(c, t) G(c+1, t)^dag, conjugated by P on the extended rows
+    // (3) U'(c, r) = G(c, t) U_mu(c, t) G(c+1, t)^dag over the extended plane,
+    // conjugated by P on the extended rows (a loop over all elements measured
+    // faster than each thread transforming the links of its own rows)
     for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
       const int cc = i % W, r = i / W;
       const int aa = cc % nm, an = aa + 1 == nm ? 0 : aa + 1;
