@@ -717,22 +717,34 @@ __global__ void __launch_bounds__(kThreads) k_wilson_rt_final(const double* part
 // quaternion products and a dot (36 FMA); the lines cost one product per
 // (site, R), shared by all T.
 //
-// One block per plane at a time: the time links are scanned in chunks of
-// kTgRows slices (local products, then a prefix over the chunks), the
-// transformed spatial links U' of the extended plane are staged in shared
-// memory, then for R = 1 .. rmax every thread extends the lines of its
-// kTgRows rows of one column a by one link, publishes them, and adds the
-// dot products with the lines kTgT rows ahead into registers acc[T]; a
-// transposing warp reduction per R folds them into the block's FP64 totals
-// in a fixed order.  Per-block sums go to `partials` in the layout
-// k_wilson_rt_final reads (one 16 x 16 chunk).
+// One block per plane at a time.  A warp owns four columns a; lane (k, c),
+// k = lane % 4, c = lane / 4, owns of column 4 warp + k the RO = Nt / 8 rows
+// c RO .. (c+1) RO - 1 (the rows its loops start from) and the extended
+// rows Nt + 2c, Nt + 2c + 1, so every lane starts loops from RO rows and
+// every row it reads beyond its own belongs to its warp: the R loop needs no
+// block barrier and no lane branches off.  The time links are scanned in
+// the same chunks of RO slices (products within a chunk, then a prefix over
+// the chunks) and the transformed spatial links U' of the extended plane are
+// staged in shared memory; then for R = 1 .. rmax every thread extends its
+// RO + 2 lines by one link, publishes them, and adds the dot products with
+// the lines 1 .. kTgT rows ahead into sixteen register accumulators (one per
+// T), which a transposing warp reduction leaves in a per-(R, warp) slot; the
+// block folds the slots into its FP64 totals in a fixed order after the
+// plane.  Rows are 2 mod 8 quaternions apart, and the rows of every other
+// chunk are shifted by tg_skew, so the 16-byte shared accesses of eight
+// lanes (two chunks of four columns) hit distinct banks.  Per-block sums go
+// to `partials` in the layout k_wilson_rt_final reads (one 16 x 16 chunk).
 // ---------------------------------------------------------------------------
 #ifndef SU2_WILSON_TG
 #define SU2_WILSON_TG 1
 #endif
-constexpr int kTgRows = 8;   // time slices (rows) a thread owns
-constexpr int kTgT = 16;     // T values in registers; also the rows added past Nt
-template <int P> struct TgThreads { static constexpr int value = P == kF64 ? 384 : 640; };
+constexpr int kTgT = 16;                 // T values in registers; also the rows added past Nt
+constexpr int kTgChunks = 8;             // row chunks of a column (lanes per column)
+constexpr int kTgCols = 32 / kTgChunks;  // columns of a warp
+constexpr int kTgExt = kTgT / kTgChunks; // extended rows a lane owns
+// block size limit (the register budget): planes of up to 64 columns in
+// FP32 / F16Q, 32 in FP64
+template <int P> struct TgThreads { static constexpr int value = P == kF64 ? 256 : 512; };
 
 template <class R> __device__ __forceinline__ Quat<R> qunit(const Quat<R>& q) {
   return qscale(q, Math<R>::rsqrt(qdot(q, q)));
@@ -749,69 +761,85 @@ __device__ __forceinline__ Site plane_site(const Geom& g, int mu, int a, int c1,
   return y;
 }
 
-template <int P>
+// Row layout of a staged plane, chunks of RO rows.  Eight lanes of a 16-byte
+// shared access are two chunks of four columns, so rows c RO + i and
+// (c+1) RO + i must start 4 mod 8 quaternions apart (16 banks), and so must
+// the extended rows Nt + 2c + e and Nt + 2c + 2 + e.  The latter needs a
+// row stride S = 2 mod 4; the former then holds for RO = 2 mod 4 and, with
+// the origin rows of odd chunks shifted by tg_skew_unit quaternions, for RO
+// = 0 mod 4 (shift 4) and RO odd (S = 2 mod 8, shift 2).  S leaves room for
+// the shift after the last column.
+template <int RO> __host__ __device__ constexpr int tg_skew_unit() { return RO % 4 == 0 ? 4 : (RO % 2 ? 2 : 0); }
+template <int RO> __host__ __device__ __forceinline__ int tg_stride(int cols) {
+  const int m = RO % 2 ? 8 : 4;
+  const int lo = cols + tg_skew_unit<RO>();
+  return lo + ((2 - lo % m) + m) % m;
+}
+template <int RO> __device__ __forceinline__ int tg_row(int r, int nt, int stride) {
+  return r * stride + (r < nt ? tg_skew_unit<RO>() * ((r / RO) & 1) : 0);
+}
+
+template <int P, int RO>
 __global__ void __launch_bounds__(TgThreads<P>::value, 1)
     k_wilson_tg(Links<P> Ls, Links<P> Lt, Geom g, int rmax, int tmax, double* partials) {
   using R = typename Real<P>::T;
-  constexpr int NTH = TgThreads<P>::value, ROWS = kTgRows;
+  constexpr int NTH = TgThreads<P>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double acc64[16 * kTgT];  // block totals; slot (R-1) kTgT + T-1
-  __shared__ R wsum[NTH / 32][kTgT];
+  __shared__ double acc64[16 * kTgT];              // block totals; slot (R-1) kTgT + T-1
+  __shared__ R wsum[16][NTH / 32][kTgT];           // per R and warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nt = g.n[3], nr = nt + kTgT;
-  const int nchunks = (nr + ROWS - 1) / ROWS, nscan = (nt + ROWS - 1) / ROWS;
+  const int nt = g.n[3], nr = nt + kTgT;           // nt = kTgChunks RO
   const int hts = g.n0h * g.st[3];
   for (int i = threadIdx.x; i < 16 * kTgT; i += blockDim.x) acc64[i] = 0.0;
   const int ntr0 = g.n[1] * g.n[2], ntr1 = g.n[0] * g.n[2], ntr2 = g.n[0] * g.n[1];
   const int nunits = ntr0 + ntr1 + ntr2;
+  const int c = lane / kTgCols, r0 = c * RO;
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int mu = u < ntr0 ? 0 : (u < ntr0 + ntr1 ? 1 : 2);
     const int tr = u - (mu == 0 ? 0 : (mu == 1 ? ntr0 : ntr0 + ntr1));
     const int nm = mu == 0 ? g.n[0] : (mu == 1 ? g.n[1] : g.n[2]);
     const int n1st = mu == 0 ? g.n[1] : g.n[0];
     const int c1 = tr % n1st, c2 = tr / n1st;
-    const int W = nm + rmax - 1;  // columns of the staged plane (column c is plane column c mod nm)
-    Quat<R>* Ue = reinterpret_cast<Quat<R>*>(smem_raw);  // Ue[r W + c] = U'(c, r), r < nr
-    Quat<R>* Sb = Ue + nr * W;                           // Sb[r nm + a]: G(a, r), then the lines S'_R(a, r)
-    Quat<R>* Ct = Sb + nr * nm;                          // Ct[k nm + a]: product of scan chunk k
-    Quat<R>* Pb = Ct + nscan * nm;                       // Pb[a] = P(a)
-    const int item = threadIdx.x;
-    const int a = item % nm, c = item / nm;
-    const bool active = c < nchunks;
-    const int r0 = c * ROWS;
+    const int W = nm + rmax - 1;       // columns of the staged plane (column cc is plane column cc mod nm)
+    const int SU = tg_stride<RO>(W), SS = tg_stride<RO>(nm);
+    Quat<R>* Ue = reinterpret_cast<Quat<R>*>(smem_raw);  // Ue[tg_row(r, SU) + cc] = U'(cc, r), r < nr
+    Quat<R>* Sb = Ue + nr * SU + 4;                      // Sb[tg_row(r, SS) + a]: G(a, r), then S'_R(a, r)
+    Quat<R>* Ct = Sb + nr * SS + 4;                      // Ct[k nm + a]: product of scan chunk k
+    Quat<R>* Pb = Ct + kTgChunks * nm;                   // Pb[a] = P(a)
+    const int a = kTgCols * warp + lane % kTgCols;
+    const bool active = a < nm;
     __syncthreads();  // the previous plane's readers are done
-    // (1) time links of this thread's rows: products within the chunk
-    if (active && r0 < nt) {
+    // (1) time links of this thread's origin rows: products within the chunk
+    if (active) {
       const Site y = plane_site(g, mu, a, c1, c2, r0);
       int h = hidx(g, y), par = parity(y);
       Quat<R> L = qone<R>();
 #pragma unroll
-      for (int i = 0; i < ROWS; ++i) {
-        if (r0 + i < nt) {
-          Sb[(r0 + i) * nm + a] = L;
-          L = qunit(qmul(L, Lt.ld(6 + par, h)));
-          h += hts;
-          par ^= 1;
-        }
+      for (int i = 0; i < RO; ++i) {
+        Sb[tg_row<RO>(r0 + i, nt, SS) + a] = L;
+        L = qunit(qmul(L, Lt.ld(6 + par, h)));
+        h += hts;
+        par ^= 1;
       }
       Ct[c * nm + a] = L;
     }
     __syncthreads();
     // (2) prefix over the chunks: G(a, r) for the thread's rows, P(a) = G(a, Nt)
-    if (active && r0 < nt) {
+    if (active) {
       Quat<R> Q = qone<R>();
       for (int k = 0; k < c; ++k) Q = qunit(qmul(Q, Ct[k * nm + a]));
       if (c > 0) {
 #pragma unroll
-        for (int i = 0; i < ROWS; ++i)
-          if (r0 + i < nt) Sb[(r0 + i) * nm + a] = qunit(qmul(Q, Sb[(r0 + i) * nm + a]));
+        for (int i = 0; i < RO; ++i) {
+          Quat<R>* p = Sb + tg_row<RO>(r0 + i, nt, SS) + a;
+          *p = qunit(qmul(Q, *p));
+        }
       }
-      if (c == nscan - 1) Pb[a] = qunit(qmul(Q, Ct[c * nm + a]));
+      if (c == kTgChunks - 1) Pb[a] = qunit(qmul(Q, Ct[c * nm + a]));
     }
     __syncthreads();
-    // (3) U'(c, r) = G(c, t) U_mu(c, t) G(c+1, t)^dag over the extended plane,
-    // conjugated by P on the extended rows (a loop over all elements measured
-    // faster than each thread transforming the links of its own rows)
+    // (3) U'(cc, r) = G(cc, t) U_mu(cc, t) G(cc+1, t)^dag over the extended
+    // plane, conjugated by P on the extended rows
     for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
       const int cc = i % W, r = i / W;
       const int aa = cc % nm, an = aa + 1 == nm ? 0 : aa + 1;
@@ -819,58 +847,60 @@ __global__ void __launch_bounds__(TgThreads<P>::value, 1)
       const int t = ext ? (r - nt) % nt : r;
       const Site y = plane_site(g, mu, aa, c1, c2, t);
       const Quat<R> lnk = Ls.ld(2 * mu + parity(y), hidx(g, y));
-      Quat<R> v = qmul_nd(qmul(Sb[t * nm + aa], lnk), Sb[t * nm + an]);
+      const int gt = tg_row<RO>(t, nt, SS);
+      Quat<R> v = qmul_nd(qmul(Sb[gt + aa], lnk), Sb[gt + an]);
       if (ext) v = qmul_nd(qmul(Pb[aa], v), Pb[an]);
-      Ue[r * W + cc] = v;
+      Ue[tg_row<RO>(r, nt, SU) + cc] = v;
     }
     __syncthreads();  // Sb now holds lines
-    // (4) R = 1 .. rmax
-    const int norig = active ? min(max(nt - r0, 0), ROWS) : 0;  // rows of this thread that start loops
-    Quat<R> own[ROWS];
+    // (4) R = 1 .. rmax, warp-synchronous.  The thread's rows start at
+    // bu / bs (origin rows, shifted by sk) and bue / bse (extended rows).
+    constexpr int unit = tg_skew_unit<RO>();
+    const int sk = unit * (c & 1);
+    const int bu = r0 * SU + sk + a, bs = r0 * SS + sk + a;
+    const int bue = (nt + kTgExt * c) * SU + a, bse = (nt + kTgExt * c) * SS + a;
+    Quat<R> own[RO];  // the origin rows' lines; the extended rows' stay in Sb
     R acc[kTgT];
 #pragma unroll
     for (int k = 0; k < kTgT; ++k) acc[k] = R(0);
     for (int Rl = 1; Rl <= rmax; ++Rl) {
       if (active) {
 #pragma unroll
-        for (int i = 0; i < ROWS; ++i) {
-          if (r0 + i < nr) {
-            const Quat<R> v = Ue[(r0 + i) * W + a + Rl - 1];
-            own[i] = Rl == 1 ? v : qmul(own[i], v);
-            Sb[(r0 + i) * nm + a] = own[i];
-          }
+        for (int i = 0; i < RO; ++i) {
+          const Quat<R> v = Ue[bu + i * SU + Rl - 1];
+          own[i] = Rl == 1 ? v : qmul(own[i], v);
+          Sb[bs + i * SS] = own[i];
+        }
+#pragma unroll
+        for (int e = 0; e < kTgExt; ++e) {
+          const Quat<R> v = Ue[bue + e * SU + Rl - 1];
+          Quat<R>* p = Sb + bse + e * SS;
+          *p = Rl == 1 ? v : qmul(*p, v);
         }
       }
-      __syncthreads();
-      if (norig == ROWS) {
-        // every row of the thread starts loops: rows r0 + 1 .. r0 + ROWS - 1 + kTgT
+      __syncwarp();
+      if (active) {
+        // origin rows r0 + i, i < RO, against rows r0 + j, j = i + T
 #pragma unroll
-        for (int j = 1; j < ROWS + kTgT; ++j) {
-          const Quat<R> w = j < ROWS ? own[j < ROWS ? j : 0] : Sb[(r0 + j) * nm + a];
+        for (int j = 1; j < RO + kTgT; ++j) {
+          Quat<R> w;
+          if (j < RO) {
+            w = own[j < RO ? j : 0];
+          } else {
+            const int rr = r0 + j;  // chunk c + j / RO while below Nt
+            w = Sb[rr * SS + (rr < nt ? unit * ((c + j / RO) & 1) : 0) + a];
+          }
 #pragma unroll
-          for (int i = 0; i < ROWS; ++i) {
+          for (int i = 0; i < RO; ++i) {
             const int T = j - i;
             if (T >= 1 && T <= kTgT && T <= tmax)
               acc[T - 1] = fma(own[i].w, w.w, fma(own[i].x, w.x, fma(own[i].y, w.y, fma(own[i].z, w.z, acc[T - 1]))));
           }
         }
-      } else if (norig > 0) {
-        // the chunk that holds slice Nt - 1: rows norig .. ROWS - 1 start no loops
-#pragma unroll
-        for (int j = 1; j < ROWS + kTgT; ++j) {
-          if (j - kTgT < norig) {
-            const Quat<R> w = j < ROWS ? own[j < ROWS ? j : 0] : Sb[(r0 + j) * nm + a];
-#pragma unroll
-            for (int i = 0; i < ROWS; ++i) {
-              const int T = j - i;
-              if (T >= 1 && T <= kTgT && T <= tmax && i < norig)
-                acc[T - 1] = fma(own[i].w, w.w, fma(own[i].x, w.x, fma(own[i].y, w.y, fma(own[i].z, w.z, acc[T - 1]))));
-            }
-          }
-        }
       }
+      __syncwarp();  // the lines are read before the next R overwrites them
       // this R's sums: a transposing butterfly leaves lanes 2k and 2k+1 the
-      // warp total of slot lo; the even lanes write it, 16 threads fold
+      // warp total of slot lo; the even lanes store it in this R's slot
       int lo = 0;
 #pragma unroll
       for (int lev = 0; lev < 4; ++lev) {
@@ -887,15 +917,17 @@ __global__ void __launch_bounds__(TgThreads<P>::value, 1)
         if (upper) lo += half;
       }
       acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
-      if ((lane & 1) == 0) wsum[warp][lo] = acc[0];
+      if ((lane & 1) == 0) wsum[Rl - 1][warp][lo] = acc[0];
 #pragma unroll
       for (int k = 0; k < kTgT; ++k) acc[k] = R(0);
-      __syncthreads();
-      if (threadIdx.x < kTgT) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += (double)wsum[w][threadIdx.x];
-        acc64[(Rl - 1) * kTgT + threadIdx.x] += t;
-      }
+    }
+    __syncthreads();
+    // the plane's sums, warps in a fixed order
+    const int nw = (int)(blockDim.x >> 5);
+    for (int s = threadIdx.x; s < rmax * kTgT; s += blockDim.x) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += (double)wsum[s / kTgT][w][s % kTgT];
+      acc64[s] += t;
     }
   }
   __syncthreads();
@@ -1151,40 +1183,40 @@ static cudaError_t launch_wilson_rt(const LatticeView& v, const void* spatial, i
   return cudaErrorInvalidValue;
 }
 
-// The temporal-gauge kernel when R and T are at most 16, a plane's columns
-// times its row chunks fit one block, and the extended plane fits in shared
-// memory; *used = false otherwise.
-template <int P>
-static cudaError_t launch_wilson_tg(const LatticeView& v, const void* spatial, int rmax, int tmax,
-                                    const Scratch& s, cudaStream_t st, bool* used) {
+// The temporal-gauge kernel when R and T are at most 16, Nt is a multiple of
+// 8 with Nt / 8 in {1, 2, 4, 6, 8}, one block holds four columns a warp of
+// the widest plane, and the staged plane fits in shared memory; *used =
+// false otherwise.
+template <int P, int RO>
+static cudaError_t launch_wilson_tg_rows(const LatticeView& v, const void* spatial, int rmax, int tmax,
+                                         const Scratch& s, cudaStream_t st, bool* used) {
   using R = typename Real<P>::T;
   constexpr int kMaxThreads = TgThreads<P>::value;
   *used = false;
-  if (!SU2_WILSON_TG || rmax > 16 || tmax > kTgT) return cudaSuccess;
   const int nmax = std::max(v.g.n[0], std::max(v.g.n[1], v.g.n[2]));
   const int nt = v.g.n[3], nr = nt + kTgT;
-  const int nchunks = (nr + kTgRows - 1) / kTgRows, nscan = (nt + kTgRows - 1) / kTgRows;
-  const int nth = (nmax * nchunks + 31) / 32 * 32;
+  const int nth = (nmax + kTgCols - 1) / kTgCols * 32;
   if (nth > kMaxThreads) return cudaSuccess;
   int dev = 0;
   cudaGetDevice(&dev);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k_wilson_tg<P>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_wilson_tg<P, RO>);
   if (e != cudaSuccess) return e;
-  const int64_t smem = ((int64_t)nr * (nmax + rmax - 1) + (int64_t)nr * nmax + (int64_t)nscan * nmax + nmax) *
+  const int64_t smem = ((int64_t)nr * tg_stride<RO>(nmax + rmax - 1) + 4 + (int64_t)nr * tg_stride<RO>(nmax) + 4 +
+                        (int64_t)kTgChunks * nmax + nmax) *
                        (int64_t)sizeof(Quat<R>);
   const int64_t dyn_max = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
   if (smem > dyn_max) return cudaSuccess;
   static bool attr_set[64] = {false};
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    e = cudaFuncSetAttribute(k_wilson_tg<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+    e = cudaFuncSetAttribute(k_wilson_tg<P, RO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson_tg<P>, nth, (size_t)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson_tg<P, RO>, nth, (size_t)smem);
   if (per_sm < 1) per_sm = 1;
   const int64_t nunits = (int64_t)v.g.n[1] * v.g.n[2] + (int64_t)v.g.n[0] * v.g.n[2] + (int64_t)v.g.n[0] * v.g.n[1];
   int64_t gx = (int64_t)device_info().sms * per_sm;
@@ -1194,13 +1226,29 @@ static cudaError_t launch_wilson_tg(const LatticeView& v, const void* spatial, i
   *used = true;
   auto Lt = links_of<P>(v.links, v.g.vh);
   auto Ls = links_of<P>(const_cast<void*>(spatial), v.g.vh);
-  k_wilson_tg<P><<<(unsigned)gx, nth, (size_t)smem, st>>>(Ls, Lt, v.g, rmax, tmax, s.partials);
+  k_wilson_tg<P, RO><<<(unsigned)gx, nth, (size_t)smem, st>>>(Ls, Lt, v.g, rmax, tmax, s.partials);
   count_launches(1);
   const int64_t V = 2 * v.g.vh;
   k_wilson_rt_final<16><<<rmax * tmax, kThreads, 0, st>>>(s.partials, (int)gx, 1, tmax, 1.0 / (3.0 * (double)V),
                                                           s.out);
   count_launches(1);
   return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_wilson_tg(const LatticeView& v, const void* spatial, int rmax, int tmax,
+                                    const Scratch& s, cudaStream_t st, bool* used) {
+  *used = false;
+  const int nt = v.g.n[3];
+  if (!SU2_WILSON_TG || rmax > 16 || tmax > kTgT || nt % kTgChunks != 0) return cudaSuccess;
+  switch (nt / kTgChunks) {
+    case 1: return launch_wilson_tg_rows<P, 1>(v, spatial, rmax, tmax, s, st, used);
+    case 2: return launch_wilson_tg_rows<P, 2>(v, spatial, rmax, tmax, s, st, used);
+    case 4: return launch_wilson_tg_rows<P, 4>(v, spatial, rmax, tmax, s, st, used);
+    case 6: return launch_wilson_tg_rows<P, 6>(v, spatial, rmax, tmax, s, st, used);
+    case 8: return launch_wilson_tg_rows<P, 8>(v, spatial, rmax, tmax, s, st, used);
+    default: return cudaSuccess;
+  }
 }
 
 cudaError_t launch_wilson(const LatticeView& v, const void* spatial, int rmax, int tmax,

@@ -273,13 +273,13 @@ def test_measurements_on_thermalised_configuration():
     lat.close()
 
 
-# Wilson loops across the kernels' limits: R and T up to 16 run the
-# temporal-gauge kernel (R = 12 and 16 here, planes that wrap a line several
-# times around a row); R = 17 or T > 16 the time-outer kernel (R = 17 needs
-# its second register chunk, which starts from prefix products; T = 18, 20 a
-# second T chunk); planes too large for one block of the temporal-gauge
-# kernel fall back to the time-outer kernel's bands or the global-memory
-# kernel.
+# Wilson loops across the kernels' limits: R and T up to 16 with Nt / 8 in
+# {1, 2, 4, 6, 8} run the temporal-gauge kernel (R = 16 here, lines that wrap
+# several times around a row); other time extents, R = 17 or T > 16 the
+# time-outer kernel (R = 17 needs its second register chunk, which starts
+# from prefix products; T = 18, 20 a second T chunk); planes too large for
+# shared memory fall back to the time-outer kernel's bands or the
+# global-memory kernel.
 _WILSON_REF = {}
 
 
@@ -287,6 +287,11 @@ _WILSON_REF = {}
 @pytest.mark.parametrize("dims,rmax,tmax", [((18, 18, 18, 4), 17, 4), ((12, 12, 12, 4), 12, 4),
                                             ((4, 4, 4, 18), 4, 18), ((6, 10, 8, 6), 6, 6),
                                             ((16, 16, 16, 8), 16, 4),
+                                            # temporal-gauge kernel, every row chunk it is built
+                                            # for (Nt / 8 = 2, 4, 6, 8 rows a lane), time lines
+                                            # wrapping past the last slice
+                                            ((4, 4, 2, 16), 2, 16), ((2, 4, 2, 32), 2, 16),
+                                            ((2, 2, 4, 48), 2, 16), ((2, 2, 2, 64), 2, 16),
                                             # 64-site rows with 96 slices: planes too large for
                                             # shared memory, so work units are bands of time
                                             # slices (76 / 60 slices in FP32, 30 / 14 in FP64)
@@ -343,8 +348,8 @@ def test_wilson_loops_both_chunkings_fp32_against_fp64_kernel():
 @pytest.mark.parametrize("prec,n,alpha", [(p, n, a) for p in ("f64", "f32", "f16q")
                                           for n, a in ((0, 0.7), (1, 0.7), (3, 0.444), (25, 0.7))
                                           if not (p == "f16q" and n > 3)])
-def test_ape_and_smeared_wilson(prec, n, alpha):
-    dims = (4, 6, 4, 6)
+@pytest.mark.parametrize("dims", [(4, 6, 4, 6), (4, 6, 4, 8)])   # time-outer and temporal-gauge kernels
+def test_ape_and_smeared_wilson(prec, n, alpha, dims):
     U = inputs.random_field(dims, 31)
     lat = Lattice(dims, 2.0, prec=prec)
     lat.set_links(U)
