@@ -325,7 +325,11 @@ int su2_ape_smear(su2_lattice* h, double alpha, int n);
  * (1/2) Tr of the R x T loop.  1 <= Rmax <= min(N0,N1,N2), 1 <= Tmax <= N3,
  * Rmax, Tmax <= 32.  use_smeared = 1 takes the spatial links from the last
  * su2_ape_smear (SU2_ESTATE if there is none since the last sweep or
- * set_links); temporal links are always the chain's.  Synchronises.
+ * set_links); temporal links are always the chain's.  For Rmax, Tmax <= 16
+ * and N3 / 8 in {1, 2, 4, 6, 8} the loops are evaluated in temporal gauge
+ * (the loop is gauge invariant: after the transform each is one dot
+ * product of two spatial lines), which equals the direct product up to
+ * rounding; other shapes multiply the loops out.  Synchronises.
  */
 int su2_wilson_loops(su2_lattice* h, int Rmax, int Tmax, int use_smeared, double* out);
 
