@@ -809,17 +809,32 @@ __global__ void __launch_bounds__(TgThreads<P>::value, 1)
     const int a = kTgCols * warp + lane % kTgCols;
     const bool active = a < nm;
     __syncthreads();  // the previous plane's readers are done
-    // (1) time links of this thread's origin rows: products within the chunk
+    // (1) this lane's links, loaded together: the time and spatial links of
+    // its origin rows (one site each) and the spatial links of the slices
+    // 2c, 2c + 1 that its extended rows repeat; then the time links'
+    // products within the chunk
+    Quat<R> us[RO + kTgExt];
     if (active) {
+      Quat<R> ut[RO];
       const Site y = plane_site(g, mu, a, c1, c2, r0);
       int h = hidx(g, y), par = parity(y);
+#pragma unroll
+      for (int i = 0; i < RO; ++i) {
+        ut[i] = Lt.ld(6 + par, h);
+        us[i] = Ls.ld(2 * mu + par, h);
+        h += hts;
+        par ^= 1;
+      }
+#pragma unroll
+      for (int e = 0; e < kTgExt; ++e) {
+        const Site ye = plane_site(g, mu, a, c1, c2, (kTgExt * c + e) % nt);
+        us[RO + e] = Ls.ld(2 * mu + parity(ye), hidx(g, ye));
+      }
       Quat<R> L = qone<R>();
 #pragma unroll
       for (int i = 0; i < RO; ++i) {
         Sb[tg_row<RO>(r0 + i, nt, SS) + a] = L;
-        L = qunit(qmul(L, Lt.ld(6 + par, h)));
-        h += hts;
-        par ^= 1;
+        L = qunit(qmul(L, ut[i]));
       }
       Ct[c * nm + a] = L;
     }
@@ -838,19 +853,24 @@ __global__ void __launch_bounds__(TgThreads<P>::value, 1)
       if (c == kTgChunks - 1) Pb[a] = qunit(qmul(Q, Ct[c * nm + a]));
     }
     __syncthreads();
-    // (3) U'(cc, r) = G(cc, t) U_mu(cc, t) G(cc+1, t)^dag over the extended
-    // plane, conjugated by P on the extended rows
-    for (int i = threadIdx.x; i < nr * W; i += blockDim.x) {
-      const int cc = i % W, r = i / W;
-      const int aa = cc % nm, an = aa + 1 == nm ? 0 : aa + 1;
-      const bool ext = r >= nt;
-      const int t = ext ? (r - nt) % nt : r;
-      const Site y = plane_site(g, mu, aa, c1, c2, t);
-      const Quat<R> lnk = Ls.ld(2 * mu + parity(y), hidx(g, y));
-      const int gt = tg_row<RO>(t, nt, SS);
-      Quat<R> v = qmul_nd(qmul(Sb[gt + aa], lnk), Sb[gt + an]);
-      if (ext) v = qmul_nd(qmul(Pb[aa], v), Pb[an]);
-      Ue[tg_row<RO>(r, nt, SU) + cc] = v;
+    // (3) U'(a, r) = G(a, t) U_mu(a, t) G(a+1, t)^dag for the lane's rows,
+    // conjugated by P on its extended rows; column a + nm (a < rmax - 1)
+    // repeats column a
+    if (active) {
+      const int an = a + 1 == nm ? 0 : a + 1;
+      const bool dup = a < rmax - 1;
+#pragma unroll
+      for (int i = 0; i < RO + kTgExt; ++i) {
+        const bool ext = i >= RO;
+        const int t = ext ? (kTgExt * c + (i - RO)) % nt : r0 + i;
+        const int r = ext ? nt + kTgExt * c + (i - RO) : r0 + i;
+        const int gt = tg_row<RO>(t, nt, SS);
+        Quat<R> v = qmul_nd(qmul(Sb[gt + a], us[i]), Sb[gt + an]);
+        if (ext) v = qmul_nd(qmul(Pb[a], v), Pb[an]);
+        const int ru = tg_row<RO>(r, nt, SU);
+        Ue[ru + a] = v;
+        if (dup) Ue[ru + a + nm] = v;
+      }
     }
     __syncthreads();  // Sb now holds lines
     // (4) R = 1 .. rmax, warp-synchronous.  The thread's rows start at

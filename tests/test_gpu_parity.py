@@ -651,6 +651,23 @@ def test_batched_barrier_timeout_is_reported():
 
 
 # ---------------------------------------------------------------------------
+def test_full_size_64_wilson_loops():
+    """W(16,16) on 64^4 FP32 in the benchmark's launch configuration (the
+    temporal-gauge kernel with eight origin rows a lane) against the FP64
+    time-outer kernel, which is pinned to the oracle, on the same links."""
+    dims = (64, 64, 64, 64)
+    a = Lattice(dims, 2.6, seed=1, start="hot", prec="f32")
+    a.sweep(2)
+    U = a.get_links()
+    w32 = a.wilson_loops(16, 16)
+    a.close()
+    b = Lattice(dims, 2.6, prec="f64")
+    b.set_links(U)
+    w64 = b.wilson_loops(16, 16)
+    b.close()
+    np.testing.assert_allclose(w32, w64, atol=1e-6, rtol=0)
+
+
 def test_full_size_64_sampled():
     """64^4 FP32 (the benchmark's lattice and launch configuration): hot start,
     one heat-bath substep and the plaquette, checked on sampled links."""
