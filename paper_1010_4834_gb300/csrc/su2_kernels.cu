@@ -14,6 +14,7 @@
 #include <atomic>
 #include <cfloat>
 #include <mutex>
+#include <type_traits>
 
 #include "su2_hb_link.cuh"
 #include "su2_internal.h"
@@ -900,23 +901,30 @@ __global__ void __launch_bounds__(TgThreads<P>::value, 1)
       }
       __syncwarp();
       if (active) {
-        // origin rows r0 + i, i < RO, against rows r0 + j, j = i + T
+        // origin rows r0 + i, i < RO, against rows r0 + j, j = i + T; the
+        // benchmark's T range (all sixteen) takes a copy without the T test
+        auto dots = [&](auto full_c) {
+          constexpr bool FULL = decltype(full_c)::value;
 #pragma unroll
-        for (int j = 1; j < RO + kTgT; ++j) {
-          Quat<R> w;
-          if (j < RO) {
-            w = own[j < RO ? j : 0];
-          } else {
-            const int rr = r0 + j;  // chunk c + j / RO while below Nt
-            w = Sb[rr * SS + (rr < nt ? unit * ((c + j / RO) & 1) : 0) + a];
-          }
+          for (int j = 1; j < RO + kTgT; ++j) {
+            Quat<R> w;
+            if (j < RO) {
+              w = own[j < RO ? j : 0];
+            } else {
+              const int rr = r0 + j;  // chunk c + j / RO while below Nt
+              w = Sb[rr * SS + (rr < nt ? unit * ((c + j / RO) & 1) : 0) + a];
+            }
 #pragma unroll
-          for (int i = 0; i < RO; ++i) {
-            const int T = j - i;
-            if (T >= 1 && T <= kTgT && T <= tmax)
-              acc[T - 1] = fma(own[i].w, w.w, fma(own[i].x, w.x, fma(own[i].y, w.y, fma(own[i].z, w.z, acc[T - 1]))));
+            for (int i = 0; i < RO; ++i) {
+              const int T = j - i;
+              if (T >= 1 && T <= kTgT && (FULL || T <= tmax))
+                acc[T - 1] =
+                    fma(own[i].w, w.w, fma(own[i].x, w.x, fma(own[i].y, w.y, fma(own[i].z, w.z, acc[T - 1]))));
+            }
           }
-        }
+        };
+        if (tmax == kTgT) dots(std::true_type{});
+        else dots(std::false_type{});
       }
       __syncwarp();  // the lines are read before the next R overwrites them
       // this R's sums: a transposing butterfly leaves lanes 2k and 2k+1 the
