@@ -731,10 +731,11 @@ __global__ void __launch_bounds__(kThreads) k_wilson_rt_final(const double* part
 // the lines 1 .. kTgT rows ahead into sixteen register accumulators (one per
 // T), which a transposing warp reduction leaves in a per-(R, warp) slot; the
 // block folds the slots into its FP64 totals in a fixed order after the
-// plane.  Rows are 2 mod 8 quaternions apart, and the rows of every other
-// chunk are shifted by tg_skew, so the 16-byte shared accesses of eight
-// lanes (two chunks of four columns) hit distinct banks.  Per-block sums go
-// to `partials` in the layout k_wilson_rt_final reads (one 16 x 16 chunk).
+// plane.  Row strides are 2 mod 4 quaternions and the origin rows of every
+// other chunk are shifted (tg_stride, tg_skew_unit), so the 16-byte shared
+// accesses of eight lanes (two chunks of four columns) hit distinct banks.
+// Per-block sums go to `partials` in the layout k_wilson_rt_final reads (one
+// 16 x 16 chunk).
 // ---------------------------------------------------------------------------
 #ifndef SU2_WILSON_TG
 #define SU2_WILSON_TG 1
