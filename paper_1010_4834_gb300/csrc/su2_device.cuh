@@ -495,12 +495,19 @@ template <int CP> struct Links<kF16Q, CP> {
   __device__ __forceinline__ Quat<float> ld(int cls, int i) const { return unpack(__ldg(at(cls, i))); }
   __device__ __forceinline__ Quat<float> ldc(int cls, int i) const { return unpack(*at(cls, i)); }
   __device__ __forceinline__ Quat<float> ldcg(int cls, int i) const { return unpack(__ldcg(at(cls, i))); }
-  static __device__ __forceinline__ Quat<float> unpack(const uint2 a) {
+  // the stored binary16 components in FP32, not yet re-normalised
+  static __device__ __forceinline__ Quat<float> unpack_raw(const uint2 a) {
     const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
     const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
-    Quat<float> q = qmake<float>(lo.x, lo.y, hi.x, hi.y);
+    return qmake<float>(lo.x, lo.y, hi.x, hi.y);
+  }
+  static __device__ __forceinline__ Quat<float> unpack(const uint2 a) {
+    const Quat<float> q = unpack_raw(a);
     return qscale(q, rsqrtf(qdot(q, q)));
   }
+  __device__ __forceinline__ Quat<float> ld_raw(int cls, int i) const { return unpack_raw(__ldg(at(cls, i))); }
+  __device__ __forceinline__ Quat<float> ldc_raw(int cls, int i) const { return unpack_raw(*at(cls, i)); }
+  __device__ __forceinline__ Quat<float> ldcg_raw(int cls, int i) const { return unpack_raw(__ldcg(at(cls, i))); }
   static __device__ __forceinline__ uint2 pack(const Quat<float>& v) {
     const __half2 lo = __floats2half2_rn(v.w, v.x);
     const __half2 hi = __floats2half2_rn(v.y, v.z);
@@ -644,6 +651,14 @@ template <int D, int S> __device__ __forceinline__ int half_step(const Geom& g, 
   return xd == 0 ? g.hwr[D] : -g.hst[D];
 }
 
+// F16Q staple loads without the per-link re-normalisation: staple_term
+// scales each product of three links once instead (see there).
+template <int P, bool NC, bool MCG, int CP>
+__device__ __forceinline__ Quat<float> ld_raw(const Links<P, CP>& L, int cls, int i) {
+  if constexpr (MCG) return L.ldcg_raw(cls, i);
+  else return NC ? L.ld_raw(cls, i) : L.ldc_raw(cls, i);
+}
+
 // The two staple terms of Section 2 Eq. 11 for link (x, MU) and one NU != MU:
 // U_nu(x) U_mu(x+nu) U_nu(x+mu)^dagger + U_nu(x-nu)^dagger U_mu(x-nu)
 // U_nu(x-nu+mu).  U_nu(x) and U_nu(x-nu+mu) have the parity p of x; the four
@@ -655,14 +670,30 @@ __device__ __forceinline__ void staple_term(const Links<P, CP>& L, const Geom& g
   using R = typename Real<P>::T;
   const int q = p ^ 1;
   const int h_mnu = h + half_step<NU, -1>(g, x);
-  const Quat<R> a = ldl<P, NC>(L, 2 * NU + p, h);                                // U_nu(x)
-  const Quat<R> b = ldmu<P, NC, MCG>(L, 2 * MU + q, h + half_step<NU, +1>(g, x)); // U_mu(x+nu)
-  const Quat<R> c = ldl<P, NC>(L, 2 * NU + q, h + dmu);                          // U_nu(x+mu)
-  const Quat<R> d = ldl<P, NC>(L, 2 * NU + q, h_mnu);                            // U_nu(x-nu)
-  const Quat<R> e = ldmu<P, NC, MCG>(L, 2 * MU + q, h_mnu);                      // U_mu(x-nu)
-  const Quat<R> f = ldl<P, NC>(L, 2 * NU + p, h_mnu + dmu);                      // U_nu(x-nu+mu)
-  qacc_mul_nd(s, qmul(a, b), c);
-  qacc_mul(s, qmul_dn(d, e), f);
+  if constexpr (P == kF16Q) {
+    // binary16 links re-normalised per term: a product of quaternions has the
+    // product of their norms, so each term of three stored links is scaled
+    // once by 1 / (|a| |b| |c|) (one rsqrt where per-link re-normalisation
+    // takes three); equal to the staple of the re-normalised links up to
+    // FP32 rounding
+    const Quat<R> a = ld_raw<P, NC, false>(L, 2 * NU + p, h);
+    const Quat<R> b = ld_raw<P, NC, MCG>(L, 2 * MU + q, h + half_step<NU, +1>(g, x));
+    const Quat<R> c = ld_raw<P, NC, false>(L, 2 * NU + q, h + dmu);
+    const Quat<R> d = ld_raw<P, NC, false>(L, 2 * NU + q, h_mnu);
+    const Quat<R> e = ld_raw<P, NC, MCG>(L, 2 * MU + q, h_mnu);
+    const Quat<R> f = ld_raw<P, NC, false>(L, 2 * NU + p, h_mnu + dmu);
+    qacc_mul_nd(s, qscale(qmul(a, b), rsqrtf(qdot(a, a) * qdot(b, b) * qdot(c, c))), c);
+    qacc_mul(s, qscale(qmul_dn(d, e), rsqrtf(qdot(d, d) * qdot(e, e) * qdot(f, f))), f);
+  } else {
+    const Quat<R> a = ldl<P, NC>(L, 2 * NU + p, h);                                // U_nu(x)
+    const Quat<R> b = ldmu<P, NC, MCG>(L, 2 * MU + q, h + half_step<NU, +1>(g, x)); // U_mu(x+nu)
+    const Quat<R> c = ldl<P, NC>(L, 2 * NU + q, h + dmu);                          // U_nu(x+mu)
+    const Quat<R> d = ldl<P, NC>(L, 2 * NU + q, h_mnu);                            // U_nu(x-nu)
+    const Quat<R> e = ldmu<P, NC, MCG>(L, 2 * MU + q, h_mnu);                      // U_mu(x-nu)
+    const Quat<R> f = ldl<P, NC>(L, 2 * NU + p, h_mnu + dmu);                      // U_nu(x-nu+mu)
+    qacc_mul_nd(s, qmul(a, b), c);
+    qacc_mul(s, qmul_dn(d, e), f);
+  }
 }
 
 // Staple sum for link (x, MU) over the directions NU != MU selected by NMASK
