@@ -1148,14 +1148,18 @@ template <int P, int RC>
 static cudaError_t launch_wilson_rt_rc(const LatticeView& v, const void* spatial, int rmax, int tmax, int tile,
                                        int smem, const Scratch& s, cudaStream_t st) {
   constexpr int NTH = kWilsonRtThreads;
-  static bool attr_set[64] = {false};
+  // the shared-memory limit is raised once per device (concurrent first
+  // calls from several host threads wait on the device's once_flag)
+  static std::once_flag attr_once[64];
+  static cudaError_t attr_err[64];
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_wilson_rt<P, RC, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kWilsonRtSmemMax);
-    if (e != cudaSuccess) return e;
-    attr_set[dev] = true;
+  if (dev >= 0 && dev < 64) {
+    std::call_once(attr_once[dev], [dev]() {
+      attr_err[dev] = cudaFuncSetAttribute(k_wilson_rt<P, RC, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kWilsonRtSmemMax);
+    });
+    if (attr_err[dev] != cudaSuccess) return attr_err[dev];
   }
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson_rt<P, RC, NTH>, NTH, smem);
@@ -1238,11 +1242,15 @@ static cudaError_t launch_wilson_tg_rows(const LatticeView& v, const void* spati
                        (int64_t)sizeof(Quat<R>);
   const int64_t dyn_max = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
   if (smem > dyn_max) return cudaSuccess;
-  static bool attr_set[64] = {false};
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-    e = cudaFuncSetAttribute(k_wilson_tg<P, RO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
-    if (e != cudaSuccess) return e;
-    attr_set[dev] = true;
+  // raised once per device, as for the time-outer kernel
+  static std::once_flag attr_once[64];
+  static cudaError_t attr_err[64];
+  if (dev >= 0 && dev < 64) {
+    const int lim = (int)dyn_max;
+    std::call_once(attr_once[dev], [dev, lim]() {
+      attr_err[dev] = cudaFuncSetAttribute(k_wilson_tg<P, RO>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    });
+    if (attr_err[dev] != cudaSuccess) return attr_err[dev];
   }
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wilson_tg<P, RO>, nth, (size_t)smem);
